@@ -1,0 +1,232 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module is the one piece shared by the CUDA path's callers (tests,
+``bench.py``) and by the oracle's tests.  It holds none of the right-hand-side,
+time-step or limiter arithmetic.  It only
+
+* describes a workload (grid, degree, gas, dissipation switches, step count),
+* draws seeded random numbers, and
+* projects analytic initial conditions onto the cell-local scaled-Legendre
+  basis (Eq. weights_equation, w_l = (1/|K|) int_K u phi_l dV) with an n+3 point
+  Gauss rule taken from ``numpy.polynomial.legendre`` (Sec. 5.1 and Sec. 6 use
+  an elevated rule for the projection).
+
+State layout: float64 ``[field][cell][mode]``, cells x-fastest, mode index
+l = l_x + (n+1)(l_y + (n+1) l_z), fields (rho, rho v_x, rho v_y, [rho v_z], e)
+and then the artificial-viscosity field alpha when ``av_on``.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, replace
+
+import numpy as np
+from numpy.polynomial import legendre as npleg
+
+BASE_SEED = 20220823
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    dim: int
+    n: int
+    N: tuple
+    lo: tuple
+    hi: tuple
+    bc: tuple = (0, 0, 0)  # 0 periodic, 1 outflow
+    gamma: float = 5.0 / 3.0
+    nu: float = 0.0
+    kappa: float = 0.0
+    av_on: int = 0
+    positivity_on: int = 0
+    cfl: float = 0.5
+    steps: int = 1
+
+    @property
+    def ncell(self) -> int:
+        return int(np.prod(self.N[: self.dim]))
+
+    @property
+    def M(self) -> int:
+        return (self.n + 1) ** self.dim
+
+    @property
+    def nfields(self) -> int:
+        return self.dim + 2 + (1 if self.av_on else 0)
+
+    @property
+    def ncons(self) -> int:
+        return self.dim + 2
+
+    @property
+    def dofs(self) -> int:
+        """conserved degrees of freedom: cells x modes x (d+2)"""
+        return self.ncell * self.M * self.ncons
+
+    @property
+    def h(self):
+        return [(self.hi[a] - self.lo[a]) / self.N[a] for a in range(self.dim)]
+
+    def shape(self):
+        return (self.nfields, self.ncell, self.M)
+
+    def with_(self, **kw) -> "Workload":
+        return replace(self, **kw)
+
+
+# ------------------------------------------------------------------ the five paper-shaped workloads
+
+def c1_density_wave(N: int = 32, n: int = 2) -> Workload:
+    """2-D Euler, gamma=5/3, periodic [0,1]^2, rho = 1 + 0.2 sin 2pi(x+y), v=(1,1), P=1."""
+    return Workload("density_wave_2d", 2, n, (N, N, 1), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), gamma=5.0 / 3.0,
+                    cfl=0.3, steps=20)
+
+
+def c2_shear_layer(N: int = 256, n: int = 3) -> Workload:
+    """2-D compressible Navier-Stokes shear layer, [0,1]x[0,2], NxN cells (h_y = 2 h_x), nu=kappa=1e-5, AV on."""
+    return Workload("ns_shear_layer_2d", 2, n, (N, N, 1), (0.0, 0.0, 0.0), (1.0, 2.0, 1.0), gamma=5.0 / 3.0,
+                    nu=1e-5, kappa=1e-5, av_on=1, cfl=0.5, steps=500)
+
+
+def c3_sod_blast(N: int = 64, n: int = 3) -> Workload:
+    """3-D rotated Sod plane + spherical blast, outflow boundaries, AV and positivity limiter on."""
+    return Workload("sod_blast_3d", 3, n, (N, N, N), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), bc=(1, 1, 1), gamma=1.4,
+                    av_on=1, positivity_on=1, cfl=0.3, steps=200)
+
+
+def c4_turbulence_box(N: int = 128, n: int = 3) -> Workload:
+    """3-D periodic subsonic turbulence box, gamma=1.001, nu=kappa=1e-4, AV on."""
+    return Workload("turbulence_box_3d", 3, n, (N, N, N), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), gamma=1.001,
+                    nu=1e-4, kappa=1e-4, av_on=1, cfl=0.5, steps=100)
+
+
+# ------------------------------------------------------------------ projection (numpy Gauss rule)
+
+def _pt_table(n: int, x: np.ndarray) -> np.ndarray:
+    """[len(x), n+1] scaled Legendre values sqrt(2l+1) P_l(x) via numpy's Legendre series."""
+    V = npleg.legvander(x, n)
+    return V * np.sqrt(2.0 * np.arange(n + 1) + 1.0)[None, :]
+
+
+def _cell_centres(wl: Workload) -> np.ndarray:
+    axes = [wl.lo[a] + (np.arange(wl.N[a]) + 0.5) * wl.h[a] for a in range(wl.dim)]
+    grids = np.meshgrid(*axes[::-1], indexing="ij")
+    return np.stack([g.reshape(-1) for g in grids[::-1]], axis=1)
+
+
+def project(wl: Workload, func, q: int | None = None, chunk: int = 1 << 15) -> np.ndarray:
+    """Project ``func(X) -> [nfields, npts]`` onto the basis of every cell (x fastest)."""
+    q = wl.n + 3 if q is None else q
+    x, g = npleg.leggauss(q)
+    B = _pt_table(wl.n, x)  # [q, n+1]
+    d = wl.dim
+    grids = np.meshgrid(*([x] * d)[::-1], indexing="ij")
+    xi = np.stack([gg.reshape(-1) for gg in grids[::-1]], axis=1)  # [q^d, d], axis 0 fastest
+    idx = np.stack([gg.reshape(-1) for gg in np.meshgrid(*([np.arange(q)] * d)[::-1], indexing="ij")[::-1]], 1)
+    G = np.prod(g[idx], axis=1)
+    midx = np.stack([gg.reshape(-1) for gg in
+                     np.meshgrid(*([np.arange(wl.n + 1)] * d)[::-1], indexing="ij")[::-1]], 1)  # [M, d]
+    phi = np.ones((xi.shape[0], wl.M))
+    for a in range(d):
+        phi *= B[idx[:, a]][:, midx[:, a]]
+    xc = _cell_centres(wl)
+    h = np.array(wl.h)
+    out = np.empty(wl.shape())
+    for c0 in range(0, wl.ncell, chunk):
+        c1 = min(wl.ncell, c0 + chunk)
+        X = xc[c0:c1, None, :] + 0.5 * h[None, None, :] * xi[None, :, :]
+        U = np.asarray(func(X.reshape(-1, d)), dtype=np.float64).reshape(-1, c1 - c0, xi.shape[0])
+        out[:, c0:c1, :] = np.einsum("fkj,j,jl->fkl", U, G, phi) / 2.0 ** d
+    return np.ascontiguousarray(out)
+
+
+def _cons(gamma, rho, vel, p, extra=None):
+    e = p / (gamma - 1.0) + 0.5 * rho * sum(v * v for v in vel)
+    fields = [rho] + [rho * v for v in vel] + [e]
+    if extra is not None:
+        fields.append(extra)
+    return np.stack(fields)
+
+
+# ------------------------------------------------------------------ initial conditions
+
+def density_wave_ic(wl: Workload, t: float = 0.0):
+    """exact solution of the advected density wave: rho(x - t, y - t), v=(1,1), P=1"""
+    def f(X):
+        x, y = X[:, 0], X[:, 1]
+        rho = 1.0 + 0.2 * np.sin(2.0 * np.pi * (x + y - 2.0 * t))
+        one = np.ones_like(x)
+        return _cons(wl.gamma, rho, [one, one], one, np.zeros_like(x) if wl.av_on else None)
+    return f
+
+
+def shear_layer_ic(wl: Workload, seed: int = BASE_SEED):
+    """smooth Kelvin-Helmholtz shear layer (Sec. 6 set-up): a=0.05, y1=0.5, y2=1.5, u_flow=1,
+    density contrast 2 (Delta rho/rho0 = 1), A=0.01, sigma=0.2, P0=10, seeded phase of the perturbation."""
+    rng = np.random.default_rng(seed)
+    phase = float(rng.uniform(0.0, 2.0 * np.pi))
+    a, y1, y2, A, sig, P0, drho = 0.05, 0.5, 1.5, 0.01, 0.2, 10.0, 1.0
+
+    def f(X):
+        x, y = X[:, 0], X[:, 1]
+        th = np.tanh((y - y1) / a) - np.tanh((y - y2) / a)
+        rho = 1.0 + drho * 0.5 * th
+        vx = 1.0 * (th - 1.0)
+        vy = A * np.sin(2.0 * np.pi * x + phase) * (np.exp(-((y - y1) ** 2) / sig**2) +
+                                                    np.exp(-((y - y2) ** 2) / sig**2))
+        p = P0 * np.ones_like(x)
+        return _cons(wl.gamma, rho, [vx, vy], p, np.zeros_like(x) if wl.av_on else None)
+    return f
+
+
+def sod_blast_ic(wl: Workload, seed: int = BASE_SEED):
+    """Sod states (1,1 | 0.125,0.1) across a plane through the box centre with a seeded unit normal,
+    plus p=100 inside a sphere of radius 0.1 around a seeded centre in [0.25,0.75]^d."""
+    rng = np.random.default_rng(seed + 3)
+    nrm = rng.normal(size=wl.dim)
+    nrm /= np.linalg.norm(nrm)
+    ctr = rng.uniform(0.25, 0.75, size=wl.dim)
+
+    def f(X):
+        s = (X - 0.5) @ nrm
+        left = s < 0.0
+        rho = np.where(left, 1.0, 0.125)
+        p = np.where(left, 1.0, 0.1)
+        r2 = np.sum((X - ctr) ** 2, axis=1)
+        p = np.where(r2 < 0.01, 100.0, p)
+        zero = np.zeros_like(rho)
+        return _cons(wl.gamma, rho, [zero] * wl.dim, p, zero if wl.av_on else None)
+    return f
+
+
+def sod_tube_ic(wl: Workload, axis: int = 0, x0: float = 0.5):
+    """planar Sod shock tube along one axis (the 1-D Riemann problem embedded in 2-D/3-D)"""
+    def f(X):
+        left = X[:, axis] < x0
+        rho = np.where(left, 1.0, 0.125)
+        p = np.where(left, 1.0, 0.1)
+        zero = np.zeros_like(rho)
+        return _cons(wl.gamma, rho, [zero] * wl.dim, p, zero if wl.av_on else None)
+    return f
+
+
+def random_modal_state(wl: Workload, seed: int, amp: float = 0.05, decay: float = 0.5,
+                       alpha_level: float = 0.3) -> np.ndarray:
+    """A physical random state for operator parity: cell means rho~1, |v|~0.3, p~1 (varying from cell to
+    cell) and higher modes drawn with amplitude amp * decay^(l_x+l_y+l_z) relative to the mean."""
+    rng = np.random.default_rng(seed)
+    d, n = wl.dim, wl.n
+    midx = np.stack([gg.reshape(-1) for gg in
+                     np.meshgrid(*([np.arange(n + 1)] * d)[::-1], indexing="ij")[::-1]], 1)
+    scale = decay ** midx.sum(1)
+    scale[0] = 0.0
+    K = wl.ncell
+    rho0 = 1.0 + 0.2 * rng.uniform(-1, 1, K)
+    vel0 = [0.3 * rng.uniform(-1, 1, K) for _ in range(d)]
+    p0 = 1.0 + 0.3 * rng.uniform(-1, 1, K)
+    mean = _cons(wl.gamma, rho0, vel0, p0, alpha_level * rng.uniform(0, 1, K) if wl.av_on else None)
+    w = np.zeros(wl.shape())
+    w[:, :, 0] = mean
+    hi = rng.uniform(-1, 1, (wl.nfields, K, wl.M)) * scale[None, None, :] * amp
+    w += hi * np.abs(mean)[:, :, None].clip(min=0.2)
+    return np.ascontiguousarray(w)
