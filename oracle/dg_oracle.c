@@ -36,7 +36,9 @@
  *    tau = f_tau h / (P c_s); the wiggle term is one value per cell per step,
  *    f_w max(0, dlogS/dt) [S > s_onset/P^2], dlogS/dt being the difference of
  *    ln S between the starts of this and the previous step over the previous
- *    step's dt (S floored at 1e-30);
+ *    step's dt, with S floored at 1e-4 s_onset/P^2 (below the floor the sensor
+ *    value is rounding noise of the higher modes, and the log of noise would
+ *    make the wiggle source noise / dt);
  *  - sensor (Eq. discontinuity_sensor2): density modes with max(l_x,l_y,l_z)=n;
  *  - time step (Eq. timestep): maxima of c_s and |v| over the volume Gauss
  *    points of the state at the start of the step, h = min_alpha h_alpha;
@@ -843,9 +845,10 @@ int or_wiggle(const or_cfg *c, const double *w, double *S_prev, double *wig, dou
     if (!S) return OR_EINVAL;
     or_sensor(c, w, S);
     double s_on = c->s_onset / ((double)g.P * g.P);
+    double s_floor = 1e-4 * s_on;
     for (long K = 0; K < g.ncell; ++K) {
         double dlog = 0.0;
-        if (step > 0 && dt_prev > 0.0) dlog = (log(fmax(S[K], 1e-30)) - log(fmax(S_prev[K], 1e-30))) / dt_prev;
+        if (step > 0 && dt_prev > 0.0) dlog = (log(fmax(S[K], s_floor)) - log(fmax(S_prev[K], s_floor))) / dt_prev;
         wig[K] = (S[K] > s_on) ? c->f_w * fmax(0.0, dlog) : 0.0;
         S_prev[K] = S[K];
     }
