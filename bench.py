@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Throughput of the DG hot path: DOF-updates/s of whole SSP-RK steps on one GB300.
+
+Workload (default): the 2-D compressible Navier-Stokes shear layer with artificial viscosity,
+256 x 256 cells on [0,1] x [0,2], degree 3 (16 modes/cell), 4 conserved fields + alpha,
+SSP(5,4), CFL 0.5, FP32-bulk arithmetic with FP64 state accumulation.  A "step" is one whole
+Runge-Kutta step: step prologue (sensor + CFL speeds), dt reduction and five fused
+right-hand-side/stage kernels.  DOF-updates per step = cells x modes x 4 conserved fields x 5 stages.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dgx|reference] [--precision fp32|fp64]
+
+Timing: W untimed steps, then K steps, each timed on the device with CUDA events recorded by the
+library around its own launches (dg_step_timed), with an L2 flush (a 256 MiB device write) before
+each timed step, outside the events.  Barrier + synchronize on both sides, max over ranks.
+N > 1 runs independent replicas (the path is sharded by whole simulations; no collective on the
+data path), `value` is the sum of the units all ranks processed over the slowest rank's time.
+--impl reference times the FP64 CPU oracle on the host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DOF-updates/s per GB300 (FP32-bulk vs FP64, same L1 error) + % HBM roofline"
+UNIT = "DOF-updates/s"
+FLUSH_BYTES = 256 << 20
+KERNEL_SRC = os.path.join(ROOT, "paper_2208_11131_gb300", "csrc", "dgx_kernels.cuh")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="dgx", choices=["dgx", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the fp64 side run, e2e and cpu baseline")
+    return ap.parse_args()
+
+
+def workload():
+    from paper_2208_11131_gb300 import inputs
+    return inputs.c2_shear_layer(N=256, n=3)
+
+
+def config_of(wl, extra=None):
+    cfg = {"workload": "ns_shear_layer_2d_256x256_deg3_av", "cells": list(wl.N[:2]), "degree": wl.n,
+           "fields": wl.nfields, "conserved_dofs": wl.dofs, "rk_stages": 5, "nu": wl.nu, "kappa": wl.kappa,
+           "gamma": wl.gamma, "cfl": wl.cfl, "l2": "flushed before every timed step (256 MiB device write)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def stage_bytes_per_value(fp32: bool):
+    """Algorithmic bytes per state value (field x cell x mode) for the five stage launches of SSP(5,4)
+    in delta form: every array a stage must read once and write once.
+      FP32-bulk: 1: u_hi, d0' | 2: u_hi, d0, d1' | 3: u_hi, d1, d2' | 4: u_hi, d2, x, d0', x' |
+                 5: u_hi, d0, x, u (FP64), u' (FP64), u_hi'   -> 4-byte words except u, u'
+      FP64:      u and every delta array are 8-byte words; no u_hi copies."""
+    if fp32:
+        return [8, 12, 12, 20, 4 + 4 + 4 + 8 + 8 + 4]
+    return [16, 24, 24, 40, 8 + 8 + 8 + 8]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-i", str(self.index), "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def traffic_for(key: str):
+    """DRAM bytes per stage launch from a committed ncu summary, if the kernel source is unchanged."""
+    try:
+        tab = json.load(open(TRAFFIC_FILE))
+    except (OSError, ValueError):
+        return None
+    ent = tab.get(key)
+    if not ent:
+        return None
+    sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+    return ent["bytes_per_launch"] if ent.get("kernel_sha256") == sha else None
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0
+    import torch.distributed as dist
+    dist.init_process_group("nccl" if os.environ.get("DGX_BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+    return dist.get_rank(), ws, int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x, ws):
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_problem(wl):
+    import oracle
+    return oracle.Problem(dim=wl.dim, n=wl.n, N=tuple(wl.N[:wl.dim]), lo=tuple(wl.lo[:wl.dim]),
+                          hi=tuple(wl.hi[:wl.dim]), bc=tuple(wl.bc[:wl.dim]), gamma=wl.gamma, nu=wl.nu,
+                          kappa=wl.kappa, av_on=wl.av_on, positivity_on=wl.positivity_on, cfl=wl.cfl)
+
+
+def run_oracle_steps(wl, w0, nsteps: int, seconds: float | None = None):
+    """time whole oracle steps; returns (seconds, steps done, threads)"""
+    import oracle
+    P = oracle_problem(wl)
+    sim = oracle.Sim(P, w0)
+    t0 = time.perf_counter()
+    done = 0
+    while done < nsteps:
+        _, st = sim.step()
+        if st != 0:
+            raise RuntimeError(f"oracle step status {st}")
+        done += 1
+        if seconds is not None and time.perf_counter() - t0 > seconds:
+            break
+    return time.perf_counter() - t0, done, oracle.num_threads()
+
+
+def reference_arm(args, rank, ws):
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+    from paper_2208_11131_gb300 import inputs
+    wl = workload()
+    w0 = inputs.project(wl, inputs.shear_layer_ic(wl))
+    run_oracle_steps(wl, w0, args.warmup)
+    secs, done, cores = run_oracle_steps(wl, w0, args.steps)
+    units = wl.dofs * 5 * done
+    value = units / secs
+    sample = f"full 256x256 grid, {done} whole SSP(5,4) steps per timed run"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": done, "warmup": args.warmup, "ms_per_step": 1e3 * secs / done, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(wl, {"engine": "FP64 CPU oracle (C, OpenMP)"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def dgx_arm(args, rank, ws, local):
+    import numpy as np
+    import torch
+
+    from paper_2208_11131_gb300 import build as B
+    from paper_2208_11131_gb300 import dgx, inputs
+
+    torch.cuda.set_device(local)
+    B.build()
+    dgx.lib()
+    wl = workload()
+    w0 = inputs.project(wl, inputs.shear_layer_ic(wl))
+    fp32 = args.precision == "fp32"
+    prec = dgx.DG_FP32_BULK if fp32 else dgx.DG_FP64
+    stream = torch.cuda.current_stream().cuda_stream
+    sim = dgx.Simulation(wl, precision=prec)
+    sim.set_stream(stream)
+    sim.set_state(w0)
+    nl = 7
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        dgx.dg_step_timed(sim.h, 0.0, nl)
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks.start()
+    time.sleep(0.25)
+    per_launch = []
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        per_launch.append(dgx.dg_step_timed(sim.h, 0.0, nl))
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    barrier(ws)
+    clk = clocks.stop()
+    sim.sync()
+    step_ms = [sum(x) for x in per_launch]
+    total_ms = allreduce_max(sum(step_ms), ws)
+    units = wl.dofs * 5 * args.steps * ws
+    value = units / (total_ms / 1e3)
+    stage_ms = sum(sum(x[2:]) for x in per_launch)
+    launches = args.steps * 5
+    bpv = stage_bytes_per_value(fp32)
+    nvals = wl.nfields * wl.ncell * wl.M
+    # per-cell wiggle source read by every stage (8 bytes per cell)
+    stage_bytes = nvals * sum(bpv) + 5 * 8 * wl.ncell
+    achieved = stage_bytes * args.steps / (stage_ms / 1e3) / 1e9
+    peaks, peak_kind = measured_peaks()
+    peak = float(peaks["hbm_gbs"])
+    key = f"stage_kernel|ns_shear_layer_2d_256x256_deg3_av|{'fp32' if fp32 else 'fp64'}"
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic_for(key), "peak_source": f"{peak_kind} hbm_gbs",
+            "algorithmic_bytes_per_launch": stage_bytes / 5,
+            "avg_launch_ms": stage_ms / launches,
+            "share_of_step": stage_ms / sum(step_ms)}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64", "data": "synthetic",
+            "config": config_of(wl, {"precision": "fp32-bulk (fp64 state and RK accumulation)" if fp32 else "fp64",
+                                     "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"}),
+            "roofline": roof, "clocks": clk, "gpu_launches": args.steps * nl,
+            "launch_ms_mean": [float(np.mean([x[i] for x in per_launch])) for i in range(nl)],
+            "wall_ms_per_step": 1e3 * t_wall / args.steps}
+
+    if not args.no_extras:
+        # end to end through the public C ABI with pinned host buffers: H2D state, one step, D2H state
+        host_in = torch.from_numpy(w0).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        a_in, a_out = host_in.numpy(), host_out.numpy()
+        e2e_steps = max(3, min(args.steps, 10))
+        dgx.dg_set_state(sim.h, a_in)
+        dgx.dg_step(sim.h, 0.0)
+        dgx.dg_get_state(sim.h, a_out)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            dgx.dg_set_state(sim.h, a_in)
+            dgx.dg_step(sim.h, 0.0)
+            dgx.dg_get_state(sim.h, a_out)
+        te = allreduce_max(time.perf_counter() - t0, ws)
+        nbytes = a_in.nbytes
+        line["e2e"] = {"value": wl.dofs * 5 * e2e_steps * ws / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                       "d2h_bytes_per_step": nbytes, "steps": e2e_steps}
+        # the other precision on the same workload, and the FP32-bulk vs FP64 difference
+        other = dgx.Simulation(wl, precision=dgx.DG_FP64 if fp32 else dgx.DG_FP32_BULK)
+        other.set_stream(stream)
+        other.set_state(w0)
+        ref = dgx.Simulation(wl, precision=prec)
+        ref.set_stream(stream)
+        ref.set_state(w0)
+        ms_other = []
+        nsteps_cmp = 10
+        for k in range(nsteps_cmp):
+            t = dgx.dg_step_timed(other.h, 0.0, nl)
+            if k >= 2:
+                ms_other.append(sum(t))
+            ref.step()
+        s_other, s_ref = other.get_state(), ref.get_state()
+        a64, a32 = (s_other, s_ref) if fp32 else (s_ref, s_other)
+        l1 = float(np.abs(a32[0] - a64[0]).sum() / np.abs(a64[0]).sum())
+        other_ms = float(np.mean(ms_other))
+        line["other_precision"] = {"dtype": "f64" if fp32 else "f32", "ms_per_step": other_ms,
+                                   "value": wl.dofs * 5 / (other_ms / 1e3), "unit": UNIT,
+                                   "steps": nsteps_cmp - 2}
+        line["fp32_vs_fp64_rel_l1_rho_after_10_steps"] = l1
+        other.close()
+        ref.close()
+        if rank == 0 and ws == 1:
+            secs, done, cores = run_oracle_steps(wl, w0, 40, seconds=15.0)
+            line["cpu_baseline"] = {"value": wl.dofs * 5 * done / secs, "unit": UNIT, "cores": cores,
+                                    "kind": "oracle",
+                                    "sample": f"full 256x256 grid, {done} whole FP64 SSP(5,4) steps"}
+    sim.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, ws, local = dist_init()
+    if args.impl == "reference":
+        reference_arm(args, rank, ws)
+    else:
+        dgx_arm(args, rank, ws, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,165 @@
+/*
+ * dgx.h -- C ABI of the GB300 (sm_103a) modal Discontinuous Galerkin hot path of
+ * Cernetic, Springel, Guillet & Pakmor, "High-order Discontinuous Galerkin
+ * hydrodynamics with sub-cell shock capturing on GPUs" (arXiv 2208.11131).
+ *
+ * One handle = one simulation on one GPU: a Cartesian grid of equal cells
+ * (Sec. 2.2), a tensor-product scaled-Legendre basis of degree n per axis
+ * (Sec. 2.3), n+1 Gauss points per axis (Sec. 2.4), the conserved fields
+ * (rho, rho v, e) of Eq. euler plus, when artificial viscosity is on, the
+ * viscosity field alpha of Sec. 4.1 as one more expanded field.
+ *
+ * State layout (host and device, all entry points): float64
+ *   w[field][cell][mode],  cell = ix + Nx*(iy + Ny*iz),
+ *   mode l = lx + (n+1)*(ly + (n+1)*lz),
+ *   fields (rho, rho vx, rho vy, [rho vz], e, [alpha]).
+ * w[f][K][0] is the cell mean (basis normalised so that (1/|K|) int phi_l phi_m = delta).
+ *
+ * Ownership: the library owns every device buffer of a handle (allocated in
+ * dg_create / dg_set_params, freed in dg_destroy).  Host and device pointers
+ * passed in are borrowed for the duration of the call only.
+ *
+ * Streams: all work of a handle is issued on its stream (default: the legacy
+ * default stream; see dg_set_stream).  Entry points that return data to the
+ * host (dg_get_state, dg_rhs, dg_max_dt, dg_conserved_sums, dg_get_aux,
+ * dg_sync) synchronise that stream; dg_step and dg_steps only enqueue work.
+ *
+ * Errors: every int-returning call returns DG_OK (0) or one of the codes
+ * below; the message of the last failure of a handle is in dg_last_error().
+ * Device-side problems (a non-positive density or pressure at a quadrature
+ * point, a non-finite time step) set a status word on the device; it is read
+ * and cleared by dg_sync / dg_get_state and reported as DG_ENONPHYS.
+ * Nothing in the library traps or asserts on the device.
+ */
+#ifndef DGX_H
+#define DGX_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dg_handle dg_t;
+
+enum {
+    DG_OK = 0,
+    DG_EINVAL = 1,       /* bad argument                                    */
+    DG_ENOMEM = 2,       /* device allocation failed                         */
+    DG_ECUDA = 3,        /* a CUDA runtime call failed                       */
+    DG_ENONPHYS = 4,     /* rho <= 0 or p <= 0 at a quadrature point (Sec. 4.2) */
+    DG_ETIMEOUT = 5,     /* a bounded device wait gave up                    */
+    DG_EUNSUPPORTED = 6  /* valid request this build does not implement      */
+};
+
+enum { DG_BC_PERIODIC = 0, DG_BC_OUTFLOW = 1 };
+enum { DG_FP64 = 0, DG_FP32_BULK = 1 };
+
+/* Cartesian grid: dim = 2 or 3; n[a] cells along axis a on [lo[a], hi[a]];
+ * bc[a] = DG_BC_PERIODIC or DG_BC_OUTFLOW (the ghost trace equals the
+ * interior trace; no dissipative flux crosses an outflow boundary). */
+typedef struct dg_grid {
+    int dim;
+    int n[3];
+    double lo[3];
+    double hi[3];
+    int bc[3];
+} dg_grid;
+
+/* Run-time parameters.  Defaults (dg_default_params) are the paper's:
+ * cfl 0.5 (Sec. 2.5, Eq. timestep), av_scale 1, f_v 2.5, f_tau 0.5, f_w 0.2,
+ * s_onset 1e-4 (Sec. 4.1; the threshold applied is s_onset / (n+1)^2).
+ *  precision: DG_FP64 (all arithmetic in FP64) or DG_FP32_BULK (quadrature,
+ *             flux and contraction arithmetic in FP32; the state u^n, the
+ *             Runge-Kutta accumulation u^{n+1} = u^n + delta, the time step
+ *             and the conservation sums in FP64).
+ *  rk_stages: 0 = the paper's choice (n+1 stages for n+1 <= 3: forward Euler,
+ *             SSP-RK2, SSP-RK3; else the 5-stage 4th-order SSP scheme), or
+ *             1, 2, 3, 5 explicitly.
+ *  av_on:     1 adds the alpha field and artificial viscosity (Sec. 4.1).
+ *  positivity_on: 1 applies the positivity limiter of Sec. 4.2 after every
+ *             stage (this build: DG_EUNSUPPORTED from dg_set_params). */
+typedef struct dg_params {
+    int precision;
+    int rk_stages;
+    double cfl;
+    int av_on;
+    double av_scale, f_v, f_tau, f_w, s_onset;
+    int positivity_on;
+} dg_params;
+
+/* Fill p with the defaults listed above (DG_FP64, automatic RK, AV off). */
+int dg_default_params(dg_params *p);
+
+/* Create a simulation: grid, polynomial degree n (0..5; the paper's order is
+ * p = n+1, Sec. 2.3), adiabatic index gamma > 1 (Eq. 3), kinematic viscosity
+ * nu >= 0 and thermal diffusivity kappa >= 0 of the Navier-Stokes flux
+ * (Sec. 3.3; both 0 gives the Euler equations).  Uses the current CUDA device.
+ * The state is zero until dg_set_state*.  *out receives the handle. */
+int dg_create(const dg_grid *grid, int degree, double gamma, double nu, double kappa, dg_t **out);
+void dg_destroy(dg_t *h);
+
+/* Change run-time parameters; (re)allocates device buffers when the field
+ * count or the precision changes, which resets the state to zero. */
+int dg_set_params(dg_t *h, const dg_params *p);
+int dg_get_params(const dg_t *h, dg_params *p);
+
+/* Sizes of the state array: fields (d+2, +1 with AV), modes per cell, cells. */
+int dg_sizes(const dg_t *h, int *nfields, int *nmodes, long long *ncells);
+
+/* Issue all further work of the handle on `stream` (a cudaStream_t). */
+int dg_set_stream(dg_t *h, void *stream);
+
+/* State in/out, layout above.  *_device variants take device pointers
+ * (float64, same layout) and copy on the handle's stream without a host sync. */
+int dg_set_state(dg_t *h, const double *host_w);
+int dg_get_state(dg_t *h, double *host_w);
+int dg_set_state_device(dg_t *h, const double *dev_w);
+int dg_get_state_device(dg_t *h, double *dev_w);
+
+/* Right-hand side L(w) = dw/dt of Eq. weight_evolution (volume integral,
+ * HLLC surface flux, recovered-gradient viscous and artificial-viscosity
+ * fluxes of Sec. 3, alpha source of Eq. timedependentviscosity) of the
+ * current state, with the per-cell wiggle term as stored (dg_set_aux).
+ * No time advance.  Output in the state layout, float64. */
+int dg_rhs(dg_t *h, double *host_out);
+int dg_rhs_device(dg_t *h, double *dev_out);
+
+/* One SSP Runge-Kutta step (Sec. 2.5).  dt > 0: that step size; dt <= 0: the
+ * CFL step of Eq. timestep from the state at the start of the step.  With AV
+ * on, the oscillation sensor (Eq. discontinuity_sensor2) and its wiggle
+ * source are updated at the start of the step.  Enqueues only. */
+int dg_step(dg_t *h, double dt);
+/* nsteps such steps, replayed from a captured CUDA graph.  Enqueues only. */
+int dg_steps(dg_t *h, int nsteps, double dt);
+
+/* One step as dg_step, timed: CUDA events are recorded on the handle's stream
+ * around each launch of the step and the call waits for the last one.
+ * ms[0] = step prologue (oscillation sensor + CFL speeds), ms[1] = time-step
+ * reduction, ms[2 + i] = fused right-hand-side / Runge-Kutta stage i.
+ * nms must be at least 2 + the stage count (at most 7).  For profiling and
+ * benchmarks; the arithmetic is identical to dg_step. */
+int dg_step_timed(dg_t *h, double dt, float *ms, int nms);
+
+/* Wait for the handle's stream and report the device status word. */
+int dg_sync(dg_t *h);
+
+/* CFL step of Eq. timestep for the current state (FP64), no time advance. */
+int dg_max_dt(dg_t *h, double *dt);
+
+/* FP64 totals sum_K |K| w[f][K][0] for the conserved fields (d+2 values). */
+int dg_conserved_sums(dg_t *h, double *out);
+
+/* Auxiliary per-cell and scalar data of the time stepper (for checkpoints
+ * and tests).  S_prev, wig: one double per cell (previous sensor value and
+ * the current wiggle source of Sec. 4.1); scal: {dt of the last step, step
+ * count, time}.  Any pointer may be NULL to skip it. */
+int dg_get_aux(dg_t *h, double *S_prev, double *wig, double *scal);
+int dg_set_aux(dg_t *h, const double *S_prev, const double *wig, const double *scal);
+
+const char *dg_last_error(const dg_t *h);
+const char *dg_status_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGX_H */

@@ -1,0 +1,764 @@
+// Host side of the C ABI declared in include/dgx.h: handle life cycle,
+// device buffers, the Runge-Kutta stage schedule, small reduction kernels and
+// CUDA-graph replay of whole steps.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "../../include/dgx.h"
+#include "dgx_internal.h"
+
+using namespace dgx;
+
+namespace {
+
+// ------------------------------------------------------------------ SSP Runge-Kutta schedules (Sec. 2.5)
+//
+// Each stage evaluates L at u^n + delta_in and forms, in "delta form",
+//   delta_out = ca delta_in + cx X + cb dt L,   X <- za delta_in + zx X + zb dt L (optional),
+// where X is an auxiliary register; the last stage commits u^{n+1} = u^n + delta_out in FP64.
+// The delta form is the Shu-Osher form rewritten with u_i = u^n + delta_i, using that the
+// coefficients of each Shu-Osher row sum to one.
+struct StageDesc {
+    double ca, cx, cb, za, zx, zb;
+    int in, out, x, write_z, last;
+};
+
+struct Schedule {
+    int stages;
+    StageDesc s[5];
+};
+
+Schedule schedule_for(int stages)
+{
+    Schedule S{};
+    S.stages = stages;
+    switch (stages) {
+    case 1:  // forward Euler
+        S.s[0] = {0, 0, 1, 0, 0, 0, -1, -1, -1, 0, 1};
+        break;
+    case 2:  // SSP-RK2 (Heun): u1 = u + dt L(u); u2 = u/2 + u1/2 + dt L(u1)/2
+        S.s[0] = {0, 0, 1, 0, 0, 0, -1, 0, -1, 0, 0};
+        S.s[1] = {0.5, 0, 0.5, 0, 0, 0, 0, -1, -1, 0, 1};
+        break;
+    case 3:  // SSP-RK3 (Shu-Osher): u2 = 3/4 u + 1/4 u1 + 1/4 dt L(u1); u3 = 1/3 u + 2/3 u2 + 2/3 dt L(u2)
+        S.s[0] = {0, 0, 1, 0, 0, 0, -1, 0, -1, 0, 0};
+        S.s[1] = {0.25, 0, 0.25, 0, 0, 0, 0, 1, -1, 0, 0};
+        S.s[2] = {2.0 / 3.0, 0, 2.0 / 3.0, 0, 0, 0, 1, -1, -1, 0, 1};
+        break;
+    case 5: {  // SSP(5,4) of Spiteri & Ruuth (2002)
+        const double b10 = 0.391752226571890;
+        const double a21 = 0.555629506348765, b21 = 0.368410593050371;
+        const double a32 = 0.379898148511597, b32 = 0.251891774271694;
+        const double a43 = 0.821920045606868, b43 = 0.544974750228521;
+        const double a52 = 0.517231671970585, a53 = 0.096059710526147, b53 = 0.063692468666290;
+        const double a54 = 0.386708617503269, b54 = 0.226007483236906;
+        S.s[0] = {0, 0, b10, 0, 0, 0, -1, 0, -1, 0, 0};          // delta1 -> D0
+        S.s[1] = {a21, 0, b21, 0, 0, 0, 0, 1, -1, 0, 0};         // delta2 -> D1
+        S.s[2] = {a32, 0, b32, 0, 0, 0, 1, 2, -1, 0, 0};         // delta3 -> D2 (delta2 kept in D1)
+        S.s[3] = {a43, 0, b43, a53, a52, b53, 2, 0, 1, 1, 0};    // delta4 -> D0, X=D1 <- a52 d2 + a53 d3 + b53 dt L3
+        S.s[4] = {a54, 1.0, b54, 0, 0, 0, 0, -1, 1, 0, 1};       // u^{n+1} = u^n + X + a54 d4 + b54 dt L4
+        break;
+    }
+    default:
+        S.stages = 0;
+    }
+    return S;
+}
+
+int auto_stages(int degree) { return degree + 1 <= 3 ? degree + 1 : 5; }
+
+__global__ void to_f32_kernel(const double *__restrict__ a, float *__restrict__ b, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+// dt from the per-block maxima of the prologue (Eq. timestep), or a fixed dt
+__global__ void dt_kernel(const double *partial, int nblk, double fixed_dt, double cfl, double hmin, int P,
+                          double *dtp, int advance, int *status)
+{
+    __shared__ double rc[256], rv[256];
+    double c = 0.0, v = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+        c = fmax(c, partial[2 * i]);
+        v = fmax(v, partial[2 * i + 1]);
+    }
+    rc[threadIdx.x] = c;
+    rv[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            rc[threadIdx.x] = fmax(rc[threadIdx.x], rc[threadIdx.x + s]);
+            rv[threadIdx.x] = fmax(rv[threadIdx.x], rv[threadIdx.x + s]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double dt = fixed_dt > 0.0 ? fixed_dt : cfl * hmin / (2.0 * P * (rc[0] + rv[0]));
+        if (!(dt > 0.0) || !isfinite(dt)) atomicOr(status, DG_STATUS_BADDT);
+        if (advance) {
+            dtp[0] = dt;
+            dtp[1] += 1.0;
+            dtp[2] += dt;
+        } else {
+            dtp[3] = dt;
+        }
+    }
+}
+
+// FP64 per-block partial sums of the cell means (fixed order => deterministic)
+__global__ void sums_kernel(const double *U, long long ncell, int M, int nc, double *partial)
+{
+    __shared__ double red[256];
+    for (int f = 0; f < nc; ++f) {
+        double s = 0.0;
+        for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ncell;
+             k += (long long)gridDim.x * blockDim.x)
+            s += U[((size_t)f * ncell + k) * M];
+        red[threadIdx.x] = s;
+        __syncthreads();
+        for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+            if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partial[blockIdx.x * nc + f] = red[0];
+        __syncthreads();
+    }
+}
+
+__global__ void sums_final_kernel(const double *partial, int nblk, int nc, double vol, double *out)
+{
+    if (threadIdx.x < nc) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += partial[b * nc + threadIdx.x];
+        out[threadIdx.x] = s * vol;
+    }
+}
+
+constexpr int kSumBlocks = 256;
+
+}  // namespace
+
+struct dg_handle {
+    dg_grid grid;
+    int degree = 0;
+    double gamma = 1.4, nu = 0.0, kappa = 0.0;
+    dg_params p;
+    int dim = 2, Q = 1, M = 1, nc = 4, nf = 4;
+    long long ncell = 0;
+    double h[3] = {1, 1, 1}, hmin = 1;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    Tables<double> td;
+    Tables<float> tf;
+    int stile[3], ptile[3], sgrid[3], pgrid[3];
+    int pblocks = 0;
+
+    double *U[2] = {nullptr, nullptr};
+    float *Uhi[2] = {nullptr, nullptr};
+    void *D[3] = {nullptr, nullptr, nullptr};
+    int cur = 0;
+    double *Sprev = nullptr, *wig = nullptr;
+    double *dtp = nullptr;  // {dt, step, t, dt query}
+    double *partial = nullptr;
+    double *sums = nullptr;  // [kSumBlocks*nc] partials + [nc] result
+    double *rhs_tmp = nullptr;
+    int *status = nullptr;
+    size_t nw = 0;
+
+    cudaGraphExec_t graph = nullptr;
+    double graph_dt = 0.0;
+
+    cudaEvent_t ev[8] = {nullptr};  // per-launch timing events of dg_step_timed
+
+    std::string err;
+};
+
+namespace {
+
+int fail(dg_t *h, int code, const char *fmt, ...)
+{
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        h->err = buf;
+    }
+    return code;
+}
+
+#define CK(h, call)                                                                             \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) return fail(h, DG_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+bool fp32(const dg_t *h) { return h->p.precision == DG_FP32_BULK; }
+size_t real_size(const dg_t *h) { return fp32(h) ? sizeof(float) : sizeof(double); }
+
+void free_buffers(dg_t *h)
+{
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(h->U[i]);
+        cudaFree(h->Uhi[i]);
+        h->U[i] = nullptr;
+        h->Uhi[i] = nullptr;
+    }
+    for (int i = 0; i < 3; ++i) {
+        cudaFree(h->D[i]);
+        h->D[i] = nullptr;
+    }
+    cudaFree(h->Sprev);
+    cudaFree(h->wig);
+    cudaFree(h->dtp);
+    cudaFree(h->partial);
+    cudaFree(h->sums);
+    cudaFree(h->rhs_tmp);
+    cudaFree(h->status);
+    h->Sprev = h->wig = h->dtp = h->partial = h->sums = h->rhs_tmp = nullptr;
+    h->status = nullptr;
+}
+
+int prepare_kernels(dg_t *h);
+
+int alloc_buffers(dg_t *h)
+{
+    free_buffers(h);
+    h->nf = h->nc + (h->p.av_on ? 1 : 0);
+    h->nw = (size_t)h->nf * h->ncell * h->M;
+    const size_t rs = real_size(h);
+    auto al = [&](void **p, size_t bytes) -> int {
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, DG_ENOMEM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+        }
+        return DG_OK;
+    };
+    int st = DG_OK;
+    for (int i = 0; i < 2 && !st; ++i) st = al((void **)&h->U[i], h->nw * sizeof(double));
+    if (fp32(h))
+        for (int i = 0; i < 2 && !st; ++i) st = al((void **)&h->Uhi[i], h->nw * sizeof(float));
+    for (int i = 0; i < 3 && !st; ++i) st = al(&h->D[i], h->nw * rs);
+    if (!st) st = al((void **)&h->Sprev, h->ncell * sizeof(double));
+    if (!st) st = al((void **)&h->wig, h->ncell * sizeof(double));
+    if (!st) st = al((void **)&h->dtp, 4 * sizeof(double));
+    int pt[3], sdummy[3];
+    if (h->dim == 2) {
+        if (fp32(h)) tiles_2d_f32(h->degree, sdummy, pt);
+        else tiles_2d_f64(h->degree, sdummy, pt);
+    } else {
+        if (fp32(h)) tiles_3d_f32(h->degree, sdummy, pt);
+        else tiles_3d_f64(h->degree, sdummy, pt);
+    }
+    for (int a = 0; a < 3; ++a) {
+        h->stile[a] = sdummy[a];
+        h->ptile[a] = pt[a];
+        const int Na = a < h->dim ? h->grid.n[a] : 1;
+        h->sgrid[a] = (Na + sdummy[a] - 1) / sdummy[a];
+        h->pgrid[a] = (Na + pt[a] - 1) / pt[a];
+    }
+    h->pblocks = h->pgrid[0] * h->pgrid[1] * h->pgrid[2];
+    if (!st) st = al((void **)&h->partial, 2 * (size_t)h->pblocks * sizeof(double));
+    if (!st) st = al((void **)&h->sums, ((size_t)kSumBlocks * h->nc + h->nc) * sizeof(double));
+    if (!st) st = al((void **)&h->status, sizeof(int));
+    if (st) {
+        free_buffers(h);
+        return st;
+    }
+    // zero state and auxiliary data
+    for (int i = 0; i < 2; ++i) CK(h, cudaMemsetAsync(h->U[i], 0, h->nw * sizeof(double), h->stream));
+    if (fp32(h))
+        for (int i = 0; i < 2; ++i) CK(h, cudaMemsetAsync(h->Uhi[i], 0, h->nw * sizeof(float), h->stream));
+    for (int i = 0; i < 3; ++i) CK(h, cudaMemsetAsync(h->D[i], 0, h->nw * rs, h->stream));
+    CK(h, cudaMemsetAsync(h->Sprev, 0, h->ncell * sizeof(double), h->stream));
+    CK(h, cudaMemsetAsync(h->wig, 0, h->ncell * sizeof(double), h->stream));
+    CK(h, cudaMemsetAsync(h->dtp, 0, 4 * sizeof(double), h->stream));
+    CK(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->cur = 0;
+    return prepare_kernels(h);
+}
+
+void base_stage_args(const dg_t *h, StageArgs &a)
+{
+    memset(&a, 0, sizeof a);
+    for (int i = 0; i < 3; ++i) {
+        a.N[i] = i < h->dim ? h->grid.n[i] : 1;
+        a.bc[i] = i < h->dim ? h->grid.bc[i] : 0;
+        a.ntile[i] = h->sgrid[i];
+        a.h[i] = h->h[i];
+    }
+    a.hmin = h->hmin;
+    a.gamma = h->gamma;
+    a.nu = h->nu;
+    a.kappa = h->kappa;
+    a.ns_on = (h->nu > 0.0 || h->kappa > 0.0) ? 1 : 0;
+    a.av_on = h->p.av_on;
+    a.av_scale = h->p.av_scale;
+    a.f_v = h->p.f_v;
+    a.f_tau = h->p.f_tau;
+    a.nf = h->nf;
+    a.ncell = h->ncell;
+    a.wig = h->wig;
+    a.dtp = h->dtp;
+    a.status = h->status;
+}
+
+cudaError_t launch_stage_any(const dg_t *h, const StageArgs &a)
+{
+    if (h->dim == 2)
+        return fp32(h) ? launch_stage_2d_f32(h->degree, a, h->tf, h->stream)
+                       : launch_stage_2d_f64(h->degree, a, h->td, h->stream);
+    return fp32(h) ? launch_stage_3d_f32(h->degree, a, h->tf, h->stream)
+                   : launch_stage_3d_f64(h->degree, a, h->td, h->stream);
+}
+
+cudaError_t launch_prologue_any(const dg_t *h, int update_sensor)
+{
+    PrologueArgs a;
+    memset(&a, 0, sizeof a);
+    for (int i = 0; i < 3; ++i) {
+        a.N[i] = i < h->dim ? h->grid.n[i] : 1;
+        a.ntile[i] = h->pgrid[i];
+    }
+    a.gamma = h->gamma;
+    a.nf = h->nf;
+    a.ncell = h->ncell;
+    a.u = fp32(h) ? (const void *)h->Uhi[h->cur] : (const void *)h->U[h->cur];
+    a.update_sensor = update_sensor && h->p.av_on;
+    a.S_prev = h->Sprev;
+    a.wig = h->wig;
+    a.dtp = h->dtp;
+    a.f_w = h->p.f_w;
+    a.s_on = h->p.s_onset / ((double)(h->degree + 1) * (h->degree + 1));
+    a.partial = h->partial;
+    a.status = h->status;
+    if (h->dim == 2)
+        return fp32(h) ? launch_prologue_2d_f32(h->degree, a, h->tf, h->stream)
+                       : launch_prologue_2d_f64(h->degree, a, h->td, h->stream);
+    return fp32(h) ? launch_prologue_3d_f32(h->degree, a, h->tf, h->stream)
+                   : launch_prologue_3d_f64(h->degree, a, h->td, h->stream);
+}
+
+// set the dynamic shared-memory attribute of this handle's kernels (launch with zero tiles)
+int prepare_kernels(dg_t *h)
+{
+    StageArgs a;
+    memset(&a, 0, sizeof a);
+    CK(h, launch_stage_any(h, a));
+    PrologueArgs pa;
+    memset(&pa, 0, sizeof pa);
+    if (h->dim == 2)
+        CK(h, fp32(h) ? launch_prologue_2d_f32(h->degree, pa, h->tf, h->stream)
+                      : launch_prologue_2d_f64(h->degree, pa, h->td, h->stream));
+    else
+        CK(h, fp32(h) ? launch_prologue_3d_f32(h->degree, pa, h->tf, h->stream)
+                      : launch_prologue_3d_f64(h->degree, pa, h->td, h->stream));
+    return DG_OK;
+}
+
+int stage_count(const dg_t *h) { return h->p.rk_stages > 0 ? h->p.rk_stages : auto_stages(h->degree); }
+
+// enqueue one full step on h->stream (no host synchronisation); with `ev`, record an event
+// before the first launch and after every launch (prologue, dt, each stage)
+int enqueue_step(dg_t *h, double dt, cudaEvent_t *ev = nullptr)
+{
+    const Schedule S = schedule_for(stage_count(h));
+    if (!S.stages) return fail(h, DG_EINVAL, "unsupported Runge-Kutta stage count %d", stage_count(h));
+    if (ev) CK(h, cudaEventRecord(ev[0], h->stream));
+    CK(h, launch_prologue_any(h, 1));
+    if (ev) CK(h, cudaEventRecord(ev[1], h->stream));
+    dt_kernel<<<1, 256, 0, h->stream>>>(h->partial, h->pblocks, dt > 0.0 ? dt : 0.0, h->p.cfl, h->hmin,
+                                        h->degree + 1, h->dtp, 1, h->status);
+    CK(h, cudaGetLastError());
+    if (ev) CK(h, cudaEventRecord(ev[2], h->stream));
+    const int c = h->cur, nx = 1 - h->cur;
+    for (int i = 0; i < S.stages; ++i) {
+        const StageDesc &d = S.s[i];
+        StageArgs a;
+        base_stage_args(h, a);
+        a.ubase = fp32(h) ? (const void *)h->Uhi[c] : (const void *)h->U[c];
+        a.din = d.in >= 0 ? h->D[d.in] : nullptr;
+        a.mode = d.last ? 2 : 1;
+        a.xbuf = d.x >= 0 ? h->D[d.x] : nullptr;
+        a.dout = d.out >= 0 ? h->D[d.out] : nullptr;
+        a.ca = d.ca;
+        a.cx = d.cx;
+        a.cb = d.cb;
+        a.za = d.za;
+        a.zx = d.zx;
+        a.zb = d.zb;
+        a.write_z = d.write_z;
+        a.uold = h->U[c];
+        a.unew = h->U[nx];
+        a.uhi_new = fp32(h) ? h->Uhi[nx] : nullptr;
+        CK(h, launch_stage_any(h, a));
+        if (ev) CK(h, cudaEventRecord(ev[3 + i], h->stream));
+    }
+    h->cur = nx;
+    return DG_OK;
+}
+
+int check_status(dg_t *h)
+{
+    int st = 0;
+    CK(h, cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (st) {
+        CK(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        if (st & DG_STATUS_NONPHYS)
+            return fail(h, DG_ENONPHYS, "non-physical state (rho <= 0 or p <= 0) at a quadrature point");
+        return fail(h, DG_ENONPHYS, "non-finite or non-positive time step");
+    }
+    return DG_OK;
+}
+
+int refresh_hi(dg_t *h)
+{
+    if (!fp32(h)) return DG_OK;
+    to_f32_kernel<<<1024, 256, 0, h->stream>>>(h->U[h->cur], h->Uhi[h->cur], h->nw);
+    CK(h, cudaGetLastError());
+    return DG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *dg_status_string(int code)
+{
+    switch (code) {
+    case DG_OK: return "ok";
+    case DG_EINVAL: return "invalid argument";
+    case DG_ENOMEM: return "out of device memory";
+    case DG_ECUDA: return "CUDA error";
+    case DG_ENONPHYS: return "non-physical state";
+    case DG_ETIMEOUT: return "device wait timed out";
+    case DG_EUNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+int dg_default_params(dg_params *p)
+{
+    if (!p) return DG_EINVAL;
+    p->precision = DG_FP64;
+    p->rk_stages = 0;
+    p->cfl = 0.5;
+    p->av_on = 0;
+    p->av_scale = 1.0;
+    p->f_v = 2.5;
+    p->f_tau = 0.5;
+    p->f_w = 0.2;
+    p->s_onset = 1e-4;
+    p->positivity_on = 0;
+    return DG_OK;
+}
+
+int dg_create(const dg_grid *grid, int degree, double gamma, double nu, double kappa, dg_t **out)
+{
+    if (!out) return DG_EINVAL;
+    *out = nullptr;
+    if (!grid || grid->dim < 2 || grid->dim > 3 || degree < 0 || degree > kMaxDegree || !(gamma > 1.0) ||
+        !(nu >= 0.0) || !(kappa >= 0.0))
+        return DG_EINVAL;
+    long long nc = 1;
+    for (int a = 0; a < grid->dim; ++a) {
+        if (grid->n[a] < 1 || !(grid->hi[a] > grid->lo[a]) || (grid->bc[a] != 0 && grid->bc[a] != 1))
+            return DG_EINVAL;
+        nc *= grid->n[a];
+    }
+    if (nc > 0x7fffffffLL) return DG_EINVAL;
+    dg_t *h = new (std::nothrow) dg_t();
+    if (!h) return DG_ENOMEM;
+    h->grid = *grid;
+    h->degree = degree;
+    h->gamma = gamma;
+    h->nu = nu;
+    h->kappa = kappa;
+    dg_default_params(&h->p);
+    h->dim = grid->dim;
+    h->Q = degree + 1;
+    h->M = 1;
+    for (int a = 0; a < h->dim; ++a) h->M *= h->Q;
+    h->nc = h->dim + 2;
+    h->ncell = nc;
+    h->hmin = 1e300;
+    for (int a = 0; a < h->dim; ++a) {
+        h->h[a] = (grid->hi[a] - grid->lo[a]) / grid->n[a];
+        if (h->h[a] < h->hmin) h->hmin = h->h[a];
+    }
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return DG_ECUDA;
+    }
+    if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return DG_ECUDA;
+    }
+    make_tables(degree, &h->td, &h->tf);
+    int st = alloc_buffers(h);
+    if (st) {
+        cudaStreamDestroy(h->cap_stream);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return DG_OK;
+}
+
+void dg_destroy(dg_t *h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    free_buffers(h);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    for (int i = 0; i < 8; ++i)
+        if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+    delete h;
+}
+
+int dg_set_params(dg_t *h, const dg_params *p)
+{
+    if (!h || !p) return DG_EINVAL;
+    if ((p->precision != DG_FP64 && p->precision != DG_FP32_BULK) || !(p->cfl > 0.0) ||
+        (p->rk_stages != 0 && p->rk_stages != 1 && p->rk_stages != 2 && p->rk_stages != 3 && p->rk_stages != 5) ||
+        (p->av_on != 0 && p->av_on != 1) || !(p->f_tau > 0.0) || p->av_scale < 0.0)
+        return fail(h, DG_EINVAL, "invalid dg_params");
+    if (p->positivity_on) return fail(h, DG_EUNSUPPORTED, "the positivity limiter is not built yet");
+    const bool realloc = p->precision != h->p.precision || p->av_on != h->p.av_on;
+    h->p = *p;
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    if (realloc) return alloc_buffers(h);
+    return DG_OK;
+}
+
+int dg_get_params(const dg_t *h, dg_params *p)
+{
+    if (!h || !p) return DG_EINVAL;
+    *p = h->p;
+    return DG_OK;
+}
+
+int dg_sizes(const dg_t *h, int *nfields, int *nmodes, long long *ncells)
+{
+    if (!h) return DG_EINVAL;
+    if (nfields) *nfields = h->nf;
+    if (nmodes) *nmodes = h->M;
+    if (ncells) *ncells = h->ncell;
+    return DG_OK;
+}
+
+int dg_set_stream(dg_t *h, void *stream)
+{
+    if (!h) return DG_EINVAL;
+    h->stream = (cudaStream_t)stream;
+    return DG_OK;
+}
+
+int dg_set_state(dg_t *h, const double *host_w)
+{
+    if (!h || !host_w) return DG_EINVAL;
+    CK(h, cudaMemcpyAsync(h->U[h->cur], host_w, h->nw * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    int st = refresh_hi(h);
+    if (st) return st;
+    CK(h, cudaStreamSynchronize(h->stream));
+    return DG_OK;
+}
+
+int dg_set_state_device(dg_t *h, const double *dev_w)
+{
+    if (!h || !dev_w) return DG_EINVAL;
+    CK(h, cudaMemcpyAsync(h->U[h->cur], dev_w, h->nw * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    return refresh_hi(h);
+}
+
+int dg_get_state(dg_t *h, double *host_w)
+{
+    if (!h || !host_w) return DG_EINVAL;
+    CK(h, cudaMemcpyAsync(host_w, h->U[h->cur], h->nw * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return check_status(h);
+}
+
+int dg_get_state_device(dg_t *h, double *dev_w)
+{
+    if (!h || !dev_w) return DG_EINVAL;
+    CK(h, cudaMemcpyAsync(dev_w, h->U[h->cur], h->nw * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    return DG_OK;
+}
+
+int dg_rhs_device(dg_t *h, double *dev_out)
+{
+    if (!h || !dev_out) return DG_EINVAL;
+    StageArgs a;
+    base_stage_args(h, a);
+    a.ubase = fp32(h) ? (const void *)h->Uhi[h->cur] : (const void *)h->U[h->cur];
+    a.din = nullptr;
+    a.mode = 0;
+    a.rhs_out = dev_out;
+    CK(h, launch_stage_any(h, a));
+    return DG_OK;
+}
+
+int dg_rhs(dg_t *h, double *host_out)
+{
+    if (!h || !host_out) return DG_EINVAL;
+    if (!h->rhs_tmp) {
+        cudaError_t e = cudaMalloc((void **)&h->rhs_tmp, h->nw * sizeof(double));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            h->rhs_tmp = nullptr;
+            return fail(h, DG_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+        }
+    }
+    int st = dg_rhs_device(h, h->rhs_tmp);
+    if (st) return st;
+    CK(h, cudaMemcpyAsync(host_out, h->rhs_tmp, h->nw * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return check_status(h);
+}
+
+int dg_step(dg_t *h, double dt)
+{
+    if (!h) return DG_EINVAL;
+    return enqueue_step(h, dt);
+}
+
+int dg_steps(dg_t *h, int nsteps, double dt)
+{
+    if (!h || nsteps < 0) return DG_EINVAL;
+    int done = 0;
+    if (h->cur != 0 && nsteps > 0) {  // bring the ping-pong parity back to 0
+        int st = enqueue_step(h, dt);
+        if (st) return st;
+        ++done;
+    }
+    if (nsteps - done >= 2) {
+        if (!h->graph || h->graph_dt != dt) {
+            if (h->graph) cudaGraphExecDestroy(h->graph);
+            h->graph = nullptr;
+            cudaStream_t user = h->stream;
+            h->stream = h->cap_stream;
+            CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+            int st = enqueue_step(h, dt);
+            if (!st) st = enqueue_step(h, dt);
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+            h->stream = user;
+            if (st) {
+                if (g) cudaGraphDestroy(g);
+                return st;
+            }
+            if (e != cudaSuccess) return fail(h, DG_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&h->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                h->graph = nullptr;
+                return fail(h, DG_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+            }
+            h->graph_dt = dt;
+        }
+        while (nsteps - done >= 2) {
+            CK(h, cudaGraphLaunch(h->graph, h->stream));
+            done += 2;
+        }
+    }
+    while (done < nsteps) {
+        int st = enqueue_step(h, dt);
+        if (st) return st;
+        ++done;
+    }
+    return DG_OK;
+}
+
+int dg_step_timed(dg_t *h, double dt, float *ms, int nms)
+{
+    if (!h || !ms) return DG_EINVAL;
+    const int nl = 2 + stage_count(h);
+    if (nms < nl) return fail(h, DG_EINVAL, "dg_step_timed needs room for %d launch times", nl);
+    for (int i = 0; i <= nl; ++i)
+        if (!h->ev[i]) CK(h, cudaEventCreate(&h->ev[i]));
+    int st = enqueue_step(h, dt, h->ev);
+    if (st) return st;
+    CK(h, cudaEventSynchronize(h->ev[nl]));
+    for (int i = 0; i < nl; ++i) CK(h, cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]));
+    return DG_OK;
+}
+
+int dg_sync(dg_t *h)
+{
+    if (!h) return DG_EINVAL;
+    return check_status(h);
+}
+
+int dg_max_dt(dg_t *h, double *dt)
+{
+    if (!h || !dt) return DG_EINVAL;
+    CK(h, launch_prologue_any(h, 0));
+    dt_kernel<<<1, 256, 0, h->stream>>>(h->partial, h->pblocks, 0.0, h->p.cfl, h->hmin, h->degree + 1, h->dtp, 0,
+                                        h->status);
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemcpyAsync(dt, h->dtp + 3, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return check_status(h);
+}
+
+int dg_conserved_sums(dg_t *h, double *out)
+{
+    if (!h || !out) return DG_EINVAL;
+    double vol = 1.0;
+    for (int a = 0; a < h->dim; ++a) vol *= h->h[a];
+    sums_kernel<<<kSumBlocks, 256, 0, h->stream>>>(h->U[h->cur], h->ncell, h->M, h->nc, h->sums);
+    sums_final_kernel<<<1, 32, 0, h->stream>>>(h->sums, kSumBlocks, h->nc, vol, h->sums + kSumBlocks * h->nc);
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemcpyAsync(out, h->sums + kSumBlocks * h->nc, h->nc * sizeof(double), cudaMemcpyDeviceToHost,
+                          h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return DG_OK;
+}
+
+int dg_get_aux(dg_t *h, double *S_prev, double *wig, double *scal)
+{
+    if (!h) return DG_EINVAL;
+    if (S_prev)
+        CK(h, cudaMemcpyAsync(S_prev, h->Sprev, h->ncell * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (wig) CK(h, cudaMemcpyAsync(wig, h->wig, h->ncell * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (scal) CK(h, cudaMemcpyAsync(scal, h->dtp, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return DG_OK;
+}
+
+int dg_set_aux(dg_t *h, const double *S_prev, const double *wig, const double *scal)
+{
+    if (!h) return DG_EINVAL;
+    if (S_prev)
+        CK(h, cudaMemcpyAsync(h->Sprev, S_prev, h->ncell * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (wig) CK(h, cudaMemcpyAsync(h->wig, wig, h->ncell * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (scal) CK(h, cudaMemcpyAsync(h->dtp, scal, 3 * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return DG_OK;
+}
+
+const char *dg_last_error(const dg_t *h)
+{
+    if (!h) return "null handle";
+    return h->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,48 @@
+// Explicit instantiation of the stage and prologue kernels for one
+// (dimension, precision) pair.  The including unit defines
+//   DGX_DIM, DGX_REAL, DGX_SUFFIX and DGX_TILES(X) with one
+//   X(degree, stage TX,TY,TZ, prologue TX,TY,TZ) entry per degree 0..5.
+#include "dgx_kernels.cuh"
+
+#define DGX_CAT2(a, b) a##b
+#define DGX_CAT(a, b) DGX_CAT2(a, b)
+
+namespace dgx {
+
+#define DGX_STAGE_CASE(n, sx, sy, sz, px, py, pz) \
+    case n:                                       \
+        return run_stage<DGX_DIM, n, DGX_REAL, sx, sy, sz>(a, t, s);
+#define DGX_PRO_CASE(n, sx, sy, sz, px, py, pz) \
+    case n:                                     \
+        return run_prologue<DGX_DIM, n, DGX_REAL, px, py, pz>(a, t, s);
+#define DGX_TILE_CASE(n, sx, sy, sz, px, py, pz) \
+    case n:                                      \
+        st[0] = sx;                              \
+        st[1] = sy;                              \
+        st[2] = sz;                              \
+        pr[0] = px;                              \
+        pr[1] = py;                              \
+        pr[2] = pz;                              \
+        return;
+
+cudaError_t DGX_CAT(launch_stage_, DGX_SUFFIX)(int degree, const StageArgs &a, const Tables<DGX_REAL> &t,
+                                               cudaStream_t s)
+{
+    switch (degree) { DGX_TILES(DGX_STAGE_CASE) }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t DGX_CAT(launch_prologue_, DGX_SUFFIX)(int degree, const PrologueArgs &a, const Tables<DGX_REAL> &t,
+                                                  cudaStream_t s)
+{
+    switch (degree) { DGX_TILES(DGX_PRO_CASE) }
+    return cudaErrorInvalidValue;
+}
+
+void DGX_CAT(tiles_, DGX_SUFFIX)(int degree, int *st, int *pr)
+{
+    switch (degree) { DGX_TILES(DGX_TILE_CASE) }
+    st[0] = st[1] = st[2] = pr[0] = pr[1] = pr[2] = 0;
+}
+
+}  // namespace dgx

@@ -1,0 +1,8 @@
+// 2-D, FP32-bulk kernels.  Tiles: stage (TX,TY,1), prologue (TX,TY,1) per degree.
+#define DGX_DIM 2
+#define DGX_REAL float
+#define DGX_SUFFIX 2d_f32
+#define DGX_TILES(X) \
+    X(0, 16, 16, 1, 16, 16, 1) X(1, 16, 8, 1, 16, 16, 1) X(2, 8, 8, 1, 16, 8, 1) \
+    X(3, 8, 4, 1, 16, 8, 1) X(4, 4, 4, 1, 8, 8, 1) X(5, 4, 4, 1, 8, 4, 1)
+#include "dgx_inst.cuh"

@@ -1,0 +1,117 @@
+// Internal declarations shared by the host API (dgx_api.cu) and the kernel
+// instantiation units (dgx_inst_*.cu).  Not part of the public C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dgx {
+
+constexpr int kMaxDegree = 5;
+// bits of the device status word
+constexpr int DG_STATUS_NONPHYS = 1;  // rho <= 0, p <= 0 or non-finite value at a quadrature point
+constexpr int DG_STATUS_BADDT = 2;    // non-finite or non-positive CFL time step
+constexpr int kMaxQ = kMaxDegree + 1;
+
+// Per-degree operator tables, host-generated in long double (dgx_tables.cu):
+//   B[i][m]  = Pt_m(x_i)                modal -> nodal (collocation at Gauss points)
+//   Dn[i][m] = l'_m(x_i)                nodal derivative on [-1,1]
+//   Wd[i][m] = g_m Dn[m][i]             transposed, Gauss-weighted derivative (weak divergence)
+//   G[i]     = g_i                      Gauss weights
+//   Lp[m], Lm[m] = l_m(+1), l_m(-1)     traces of the nodal Lagrange basis
+//   Cm[m], Cp[m]  recovered value at the interface from the left / right cell's nodal line
+//   Dm[m], Dp[m]  recovered normal derivative (multiply by 1/(f h)) from left / right cell
+// All indices run over Q = n+1 entries; arrays are sized for the largest degree.
+template <typename Real>
+struct Tables {
+    Real B[kMaxQ][kMaxQ];
+    Real Dn[kMaxQ][kMaxQ];
+    Real Wd[kMaxQ][kMaxQ];
+    Real G[kMaxQ];
+    Real Lp[kMaxQ], Lm[kMaxQ];
+    Real Cm[kMaxQ], Cp[kMaxQ];
+    Real Dm[kMaxQ], Dp[kMaxQ];
+    Real inv_f;  // 1/f, f the recovery overlap fraction
+};
+
+void make_tables(int degree, Tables<double> *td, Tables<float> *tf);
+
+// Arguments of the fused right-hand-side / Runge-Kutta stage kernel.
+struct StageArgs {
+    int N[3];      // cells per axis (1 for unused axes)
+    int bc[3];     // 0 periodic, 1 outflow
+    int ntile[3];  // tiles per axis
+    double h[3];
+    double hmin;
+    double gamma, nu, kappa;
+    int ns_on;  // nu > 0 or kappa > 0
+    int av_on;
+    double av_scale, f_v, f_tau;
+    int nf;  // fields incl. alpha
+    long long ncell;
+
+    // stage input state = ubase + din (din may be null: delta = 0)
+    const void *ubase;  // Real*: FP32 high copy of u^n (bulk) or u^n itself (FP64)
+    const void *din;    // Real*
+    const double *wig;  // per cell wiggle source
+    const double *dtp;  // device scalars {dt, step, t}
+
+    // epilogue
+    int mode;  // 0: write L to rhs_out; 1: delta stage; 2: last stage (commit u^{n+1})
+    double *rhs_out;
+    void *xbuf;  // Real*: auxiliary register read (cx, zx) and written (write_z)
+    void *dout;  // Real*
+    double ca, cx, cb, za, zx, zb;
+    int write_z;
+    const double *uold;  // FP64 u^n
+    double *unew;        // FP64 u^{n+1}
+    float *uhi_new;      // FP32 copy of u^{n+1} (bulk mode) or null
+
+    int *status;
+};
+
+// Arguments of the step-prologue kernel (CFL speeds + oscillation sensor).
+struct PrologueArgs {
+    int N[3];
+    int ntile[3];
+    double gamma;
+    int nf;
+    long long ncell;
+    const void *u;  // Real*
+    int update_sensor;
+    double *S_prev;
+    double *wig;
+    const double *dtp;
+    double f_w, s_on;
+    double *partial;  // [blocks][2] max c_s, max |v|
+    int *status;
+};
+
+struct LaunchCfg {
+    int blocks;
+    int threads;
+    size_t smem;
+};
+
+// Kernel launchers (defined in the instantiation units).  `prec` 0 = FP64, 1 = FP32.
+cudaError_t launch_stage(int dim, int degree, int prec, const StageArgs &a, const Tables<double> &td,
+                         const Tables<float> &tf, cudaStream_t s);
+cudaError_t launch_prologue(int dim, int degree, int prec, const PrologueArgs &a, const Tables<double> &td,
+                            const Tables<float> &tf, cudaStream_t s, int *nblocks_out);
+void stage_tiles(int dim, int degree, int prec, int tile[3]);
+void prologue_tiles(int dim, int degree, int prec, int tile[3]);
+
+cudaError_t launch_stage_2d_f64(int degree, const StageArgs &a, const Tables<double> &t, cudaStream_t s);
+cudaError_t launch_stage_2d_f32(int degree, const StageArgs &a, const Tables<float> &t, cudaStream_t s);
+cudaError_t launch_stage_3d_f64(int degree, const StageArgs &a, const Tables<double> &t, cudaStream_t s);
+cudaError_t launch_stage_3d_f32(int degree, const StageArgs &a, const Tables<float> &t, cudaStream_t s);
+cudaError_t launch_prologue_2d_f64(int degree, const PrologueArgs &a, const Tables<double> &t, cudaStream_t s);
+cudaError_t launch_prologue_2d_f32(int degree, const PrologueArgs &a, const Tables<float> &t, cudaStream_t s);
+cudaError_t launch_prologue_3d_f64(int degree, const PrologueArgs &a, const Tables<double> &t, cudaStream_t s);
+cudaError_t launch_prologue_3d_f32(int degree, const PrologueArgs &a, const Tables<float> &t, cudaStream_t s);
+void tiles_2d_f64(int degree, int *stage, int *pro);
+void tiles_2d_f32(int degree, int *stage, int *pro);
+void tiles_3d_f64(int degree, int *stage, int *pro);
+void tiles_3d_f32(int degree, int *stage, int *pro);
+
+}  // namespace dgx

@@ -1,0 +1,860 @@
+// Device code of the modal DG right-hand side and SSP-RK stage update
+// (arXiv 2208.11131, Sec. 2-4), written for sm_103a.
+//
+// Formulation.  Each CTA owns a tile of cells plus the face-neighbour halo.
+// The stage state is loaded once into shared memory and turned from modal
+// weights into values at the (n+1)^d Gauss points by d sum-factorised 1-D
+// passes (B[i][m] = Pt_m(x_i)).  Because n+1 Gauss points integrate the
+// modal mass matrix exactly, every modal sum of Eq. time_stepping_final has
+// an exact nodal counterpart:
+//   volume:   sum_j g_j d_alpha phi_l(x_j) F_alpha(x_j)
+//             = sum_m B-transforms of  r(m) = sum_i g_i Dn[i][m_alpha] F_alpha(i)
+//   faces:    phi_l(+-1, x_k) = sum_m l_m(+-1) B[m][l_alpha] phi_t(x_k),
+//   sources:  projection = B-transform of g_j s(x_j),
+// so the kernel accumulates a nodal residual r and applies the transposed
+// transform once at the end.  Interface recovery (Sec. 3.2, Eq.
+// basisprojection) reduces to four 1-D functionals on the nodal lines normal
+// to a face (Cm/Cp: recovered value, Dm/Dp: recovered normal derivative);
+// tangential derivatives of the recovered state apply the nodal derivative
+// along the face.  Both CTAs that share a tile-boundary face compute its flux
+// with the same code from the same data, so the flux is bitwise identical on
+// both sides and the scheme stays conservative without atomics.
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+
+#include "dgx_internal.h"
+
+namespace dgx {
+
+// ------------------------------------------------------------------ tile shape
+
+template <int DIM, int N, int TX, int TY, int TZ>
+struct Shape {
+    static constexpr int Q = N + 1;
+    static constexpr int NP = DIM == 2 ? Q * Q : Q * Q * Q;  // nodes (= modes) per cell
+    static constexpr int NPF = DIM == 2 ? Q : Q * Q;         // nodes per face
+    static constexpr int NC = DIM + 2;                       // conserved fields
+    static constexpr int NFM = DIM + 3;                      // + alpha
+    static constexpr int TC = TX * TY * TZ;
+    __host__ __device__ static constexpr int T(int a) { return a == 0 ? TX : (a == 1 ? TY : TZ); }
+    __host__ __device__ static constexpr int HB(int a) { return TC / T(a); }
+    static constexpr int NHALO = 2 * (HB(0) + HB(1) + (DIM == 3 ? HB(2) : 0));
+    static constexpr int NSLOT = TC + NHALO;
+    __host__ __device__ static constexpr int HOFF(int a, int s)
+    {
+        return TC + (a > 0 ? 2 * HB(0) : 0) + (a > 1 ? 2 * HB(1) : 0) + s * HB(a);
+    }
+    __host__ __device__ static constexpr int NFA(int a) { return (T(a) + 1) * HB(a); }
+    __host__ __device__ static constexpr int FOFF(int a) { return (a > 0 ? NFA(0) : 0) + (a > 1 ? NFA(1) : 0); }
+    static constexpr int NFACE = NFA(0) + NFA(1) + (DIM == 3 ? NFA(2) : 0);
+    __host__ __device__ static constexpr int S(int a) { return a == 0 ? 1 : (a == 1 ? Q : Q * Q); }
+
+    // transverse tile index of a tile cell with respect to axis a
+    __device__ static int trans(int a, int cx, int cy, int cz)
+    {
+        return a == 0 ? cy + TY * cz : (a == 1 ? cx + TX * cz : cx + TX * cy);
+    }
+    __device__ static void untrans(int a, int t, int *c)
+    {
+        if (a == 0) {
+            c[1] = t % TY;
+            c[2] = t / TY;
+        } else if (a == 1) {
+            c[0] = t % TX;
+            c[2] = t / TX;
+        } else {
+            c[0] = t % TX;
+            c[1] = t / TX;
+        }
+    }
+    // transverse node index k of node j w.r.t. axis a (face numbering, increasing axes)
+    __device__ static int ktrans(int a, int j)
+    {
+        if (DIM == 2) return a == 0 ? j / Q : j % Q;
+        return a == 0 ? j / Q : (a == 1 ? (j % Q) + Q * (j / (Q * Q)) : j % (Q * Q));
+    }
+    // node index from position i along a and transverse node k
+    __device__ static int knode(int a, int i, int k)
+    {
+        if (DIM == 2) return a == 0 ? i + Q * k : k + Q * i;
+        return a == 0 ? i + Q * k : (a == 1 ? (k % Q) + Q * i + Q * Q * (k / Q) : k + Q * Q * i);
+    }
+};
+
+// ------------------------------------------------------------------ pointwise physics (Sec. 2.1, 3.3, 4.1)
+
+template <typename Real>
+__device__ __forceinline__ Real clamp01(Real a)
+{
+    return a < Real(0) ? Real(0) : (a > Real(1) ? Real(1) : a);
+}
+
+// primitive variables; returns false for rho <= 0, p <= 0 or non-finite values
+template <int DIM, typename Real>
+__device__ __forceinline__ bool primitives(const Real *u, Real gamma, Real &rho, Real *v, Real &p, Real &cs)
+{
+    rho = u[0];
+    const Real inv = Real(1) / rho;
+    Real ke = Real(0);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        v[a] = u[1 + a] * inv;
+        ke += u[1 + a] * v[a];
+    }
+    p = (gamma - Real(1)) * (u[DIM + 1] - Real(0.5) * ke);
+    const bool ok = (rho > Real(0)) && (p > Real(0));
+    cs = ok ? sqrt(gamma * p * inv) : Real(0);
+    return ok;
+}
+
+template <int DIM, typename Real>
+__device__ __forceinline__ void euler_flux(const Real *u, const Real *v, Real p, int a, Real *F)
+{
+    const Real va = v[a];
+    F[0] = u[1 + a];
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) F[1 + b] = u[1 + b] * va + (b == a ? p : Real(0));
+    F[DIM + 1] = (u[DIM + 1] + p) * va;
+}
+
+// HLLC with Davis wave speeds (Toro); passive transverse momentum.  Returns false on a bad state.
+template <int DIM, typename Real>
+__device__ __forceinline__ bool hllc(const Real *uL, const Real *uR, Real gamma, int a, Real *F)
+{
+    Real rL, rR, pL, pR, cL, cR, vL[3], vR[3];
+    bool ok = primitives<DIM>(uL, gamma, rL, vL, pL, cL);
+    ok = primitives<DIM>(uR, gamma, rR, vR, pR, cR) && ok;
+    const Real SL = fmin(vL[a] - cL, vR[a] - cR);
+    const Real SR = fmax(vL[a] + cL, vR[a] + cR);
+    if (SL >= Real(0)) {
+        euler_flux<DIM>(uL, vL, pL, a, F);
+        return ok;
+    }
+    if (SR < Real(0)) {
+        euler_flux<DIM>(uR, vR, pR, a, F);
+        return ok;
+    }
+    const Real num = pR - pL + rL * vL[a] * (SL - vL[a]) - rR * vR[a] * (SR - vR[a]);
+    const Real den = rL * (SL - vL[a]) - rR * (SR - vR[a]);
+    const Real Ss = num / den;
+    const bool left = Ss >= Real(0);
+    const Real *uK = left ? uL : uR;
+    const Real *vK = left ? vL : vR;
+    const Real rK = left ? rL : rR, pK = left ? pL : pR, SK = left ? SL : SR;
+    euler_flux<DIM>(uK, vK, pK, a, F);
+    const Real fac = rK * (SK - vK[a]) / (SK - Ss);
+    Real us[DIM + 2];
+    us[0] = fac;
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) us[1 + b] = fac * (b == a ? Ss : vK[b]);
+    us[DIM + 1] = fac * (uK[DIM + 1] / rK + (Ss - vK[a]) * (Ss + pK / (rK * (SK - vK[a]))));
+#pragma unroll
+    for (int f = 0; f < DIM + 2; ++f) F[f] += SK * (us[f] - uK[f]);
+    return ok;
+}
+
+// Navier-Stokes flux along axis a (Sec. 3.3): (0, Pi_a, v.Pi_a + kappa (gamma-1) rho d_a u_int),
+// Pi = nu rho (grad v + grad v^T - 2/3 div v I).  grad[b][f] is the physical gradient.
+template <int DIM, typename Real>
+__device__ __forceinline__ void ns_flux(const Real *u, const Real (*grad)[DIM + 2], Real gamma, Real nu, Real kappa,
+                                        int a, Real *F)
+{
+    const Real rho = u[0];
+    const Real inv = Real(1) / rho;
+    Real v[DIM], dv[DIM][DIM];
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) v[b] = u[1 + b] * inv;
+    Real div = Real(0);
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) dv[b][c] = (grad[b][1 + c] - v[c] * grad[b][0]) * inv;
+        div += dv[b][b];
+    }
+    const Real nr = nu * rho;
+    Real work = Real(0);
+    F[0] = Real(0);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+        Real pi = nr * (dv[a][c] + dv[c][a] - (c == a ? Real(2.0 / 3.0) * div : Real(0)));
+        F[1 + c] = pi;
+        work += v[c] * pi;
+    }
+    Real duint = (grad[a][DIM + 1] - u[DIM + 1] * inv * grad[a][0]) * inv;
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) duint -= v[c] * dv[a][c];
+    F[DIM + 1] = work + kappa * (gamma - Real(1)) * rho * duint;
+}
+
+// ------------------------------------------------------------------ shared memory plan
+
+template <int DIM, int N, typename Real, int TX, int TY, int TZ>
+struct StagePlan {
+    using S = Shape<DIM, N, TX, TY, TZ>;
+    static constexpr int Q = S::Q;
+    static constexpr int TAB = 3 * Q * Q + 7 * Q + 1;
+    static constexpr int SZ_U = S::NFM * S::NSLOT * S::NP;
+    static constexpr int SZ_F = DIM * S::NC * S::TC * S::NP;
+    static constexpr int SZ_W = SZ_U > SZ_F ? SZ_U : SZ_F;
+    static constexpr int SZ_R = S::NFM * S::TC * S::NP;
+    static constexpr int SZ_FACE = S::NC * S::NFACE * S::NPF;
+    static constexpr int OFF_U = (TAB + 3) / 4 * 4;
+    static constexpr int OFF_W = OFF_U + SZ_U;
+    static constexpr int OFF_R = OFF_W + SZ_W;
+    static constexpr int OFF_UT = OFF_R + SZ_R;
+    static constexpr int OFF_FH = OFF_UT + SZ_FACE;
+    static constexpr int OFF_WIG = OFF_FH + SZ_FACE;
+    static constexpr int NREAL = OFF_WIG + (S::TC + 3) / 4 * 4;
+    static constexpr size_t BYTES = sizeof(Real) * (size_t)NREAL + sizeof(int) * (size_t)S::NSLOT;
+};
+
+template <int DIM, int N, typename Real, int TX, int TY, int TZ>
+struct ProloguePlan {
+    using S = Shape<DIM, N, TX, TY, TZ>;
+    static constexpr int Q = S::Q;
+    static constexpr int TAB = (Q * Q + 3) / 4 * 4;
+    static constexpr int SZ = S::NC * S::TC * S::NP;
+    static constexpr int NREAL = TAB + 2 * SZ;
+    static constexpr size_t BYTES = sizeof(Real) * (size_t)NREAL + sizeof(int) * (size_t)S::TC;
+};
+
+template <typename Real>
+__device__ __forceinline__ Real ld_cg(const Real *p)
+{
+    return *p;
+}
+
+// global cell index of a tile slot (tile cell or face-neighbour halo), -1 if none
+template <class S>
+__device__ __forceinline__ int slot_global(int slot, const int *o, const int *V, const int *N, const int *bc)
+{
+    constexpr int TX = S::T(0), TY = S::T(1);
+    int c[3];
+    if (slot < S::TC) {
+        c[0] = slot % TX;
+        c[1] = (slot / TX) % TY;
+        c[2] = slot / (TX * TY);
+        if (c[0] >= V[0] || c[1] >= V[1] || c[2] >= V[2]) return -1;
+        return (o[0] + c[0]) + N[0] * ((o[1] + c[1]) + N[1] * (o[2] + c[2]));
+    }
+    int r = slot - S::TC;
+    int a = 0;
+    for (; a < 3; ++a) {
+        if (r < 2 * S::HB(a)) break;
+        r -= 2 * S::HB(a);
+    }
+    const int s = r / S::HB(a);
+    const int t = r % S::HB(a);
+    c[0] = c[1] = c[2] = 0;
+    S::untrans(a, t, c);
+    int g[3];
+    for (int b = 0; b < 3; ++b) {
+        if (b == a) continue;
+        if (c[b] >= V[b]) return -1;
+        g[b] = o[b] + c[b];
+    }
+    int ca = s == 0 ? o[a] - 1 : o[a] + V[a];
+    if (ca < 0 || ca >= N[a]) {
+        if (bc[a] != 0) return -1;
+        ca = (ca + N[a]) % N[a];
+    }
+    g[a] = ca;
+    return g[0] + N[0] * (g[1] + N[1] * g[2]);
+}
+
+// ------------------------------------------------------------------ the fused stage kernel
+
+template <int DIM, int N, typename Real, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(256) stage_kernel(const StageArgs A, const Tables<Real> Tg)
+{
+    using S = Shape<DIM, N, TX, TY, TZ>;
+    using PL = StagePlan<DIM, N, Real, TX, TY, TZ>;
+    constexpr int Q = S::Q, NP = S::NP, NPF = S::NPF, NC = S::NC, TC = S::TC, NSLOT = S::NSLOT;
+    constexpr int NFACE = S::NFACE;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real *sm = reinterpret_cast<Real *>(smem_raw);
+    Real *tB = sm, *tDn = tB + Q * Q, *tWd = tDn + Q * Q, *tG = tWd + Q * Q;
+    Real *tLp = tG + Q, *tLm = tLp + Q, *tCm = tLm + Q, *tCp = tCm + Q, *tDm = tCp + Q, *tDp = tDm + Q;
+    Real *sU = sm + PL::OFF_U, *sW = sm + PL::OFF_W, *sR = sm + PL::OFF_R;
+    Real *sUt = sm + PL::OFF_UT, *sFh = sm + PL::OFF_FH, *sWig = sm + PL::OFF_WIG;
+    int *sG = reinterpret_cast<int *>(sm + PL::NREAL);
+    __shared__ int s_status;
+
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int nf = A.nf;
+    const bool av = A.av_on != 0, ns = A.ns_on != 0;
+    const bool need_grad = av || ns;
+
+    int b = blockIdx.x;
+    const int tx = b % A.ntile[0];
+    b /= A.ntile[0];
+    const int ty = b % A.ntile[1];
+    const int tz = b / A.ntile[1];
+    const int o[3] = {tx * TX, ty * TY, tz * TZ};
+    const int V[3] = {min(TX, A.N[0] - o[0]), min(TY, A.N[1] - o[1]), DIM == 3 ? min(TZ, A.N[2] - o[2]) : 1};
+
+    for (int i = tid; i < Q * Q; i += nth) {
+        tB[i] = Tg.B[i / Q][i % Q];
+        tDn[i] = Tg.Dn[i / Q][i % Q];
+        tWd[i] = Tg.Wd[i / Q][i % Q];
+    }
+    for (int i = tid; i < Q; i += nth) {
+        tG[i] = Tg.G[i];
+        tLp[i] = Tg.Lp[i];
+        tLm[i] = Tg.Lm[i];
+        tCm[i] = Tg.Cm[i];
+        tCp[i] = Tg.Cp[i];
+        tDm[i] = Tg.Dm[i];
+        tDp[i] = Tg.Dp[i];
+    }
+    for (int s = tid; s < NSLOT; s += nth) sG[s] = slot_global<S>(s, o, V, A.N, A.bc);
+    if (tid == 0) s_status = 0;
+    __syncthreads();
+
+    // ---- load the stage state (u^n [+ delta]) of tile and halo cells
+    {
+        const Real *ub = static_cast<const Real *>(A.ubase);
+        const Real *di = static_cast<const Real *>(A.din);
+        const int total = nf * NSLOT * NP;
+        for (int idx = tid; idx < total; idx += nth) {
+            const int l = idx % NP;
+            const int fs = idx / NP;
+            const int slot = fs % NSLOT, f = fs / NSLOT;
+            const int g = sG[slot];
+            Real v = Real(0);
+            if (g >= 0) {
+                const size_t gi = ((size_t)f * A.ncell + g) * NP + l;
+                v = ub[gi];
+                if (di) v += di[gi];
+            }
+            sU[idx] = v;
+        }
+        for (int c = tid; c < TC; c += nth) sWig[c] = (av && sG[c] >= 0) ? (Real)A.wig[sG[c]] : Real(0);
+    }
+    __syncthreads();
+
+    // ---- modal -> nodal, d sum-factorised passes over all fields and slots
+    {
+        Real *src = sU, *dst = sW;
+        const int total = nf * NSLOT * NP;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            const int Sa = S::S(a);
+            for (int idx = tid; idx < total; idx += nth) {
+                const int j = idx % NP;
+                const int fs = idx / NP;
+                if (sG[fs % NSLOT] < 0) continue;
+                const int i = (j / Sa) % Q;
+                const Real *p = src + fs * NP + (j - i * Sa);
+                Real acc = Real(0);
+#pragma unroll
+                for (int m = 0; m < Q; ++m) acc = fma(tB[i * Q + m], p[m * Sa], acc);
+                dst[idx] = acc;
+            }
+            Real *t = src;
+            src = dst;
+            dst = t;
+            __syncthreads();
+        }
+        if (DIM == 3) {  // result landed in sW: move it back to sU
+            for (int idx = tid; idx < total; idx += nth) sU[idx] = sW[idx];
+            __syncthreads();
+        }
+    }
+
+    const Real gamma = (Real)A.gamma, nu = (Real)A.nu, kappa = (Real)A.kappa;
+    const Real P = (Real)(N + 1);
+    const Real epsfac = (Real)(A.av_scale * A.hmin / (N + 1));
+    const Real inv_tau = (Real)((N + 1) / (A.f_tau * A.hmin));  // times c_s
+    const Real f_v = (Real)A.f_v;
+    Real two_h[3], cax[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        two_h[a] = (Real)(2.0 / A.h[a]);
+        cax[a] = (Real)((DIM == 2 ? 0.5 : 0.25) / A.h[a]);
+    }
+    const Real src_w = (Real)(DIM == 2 ? 0.25 : 0.125);
+    (void)P;
+    int bad = 0;
+
+    // ---- pointwise volume fluxes (Euler - NS - AV) and the alpha source
+    {
+        for (int idx = tid; idx < TC * NP; idx += nth) {
+            const int c = idx / NP, j = idx % NP;
+            if (sG[c] < 0) continue;
+            Real u[NC + 1];
+#pragma unroll
+            for (int f = 0; f < NC; ++f) u[f] = sU[(f * NSLOT + c) * NP + j];
+            u[NC] = av ? sU[(NC * NSLOT + c) * NP + j] : Real(0);
+            Real gr[DIM][NC];
+            if (need_grad) {
+#pragma unroll
+                for (int a = 0; a < DIM; ++a) {
+                    const int Sa = S::S(a);
+                    const int i = (j / Sa) % Q;
+                    const int base = j - i * Sa;
+#pragma unroll
+                    for (int f = 0; f < NC; ++f) {
+                        const Real *p = sU + (f * NSLOT + c) * NP + base;
+                        Real acc = Real(0);
+#pragma unroll
+                        for (int m = 0; m < Q; ++m) acc = fma(tDn[i * Q + m], p[m * Sa], acc);
+                        gr[a][f] = acc * two_h[a];
+                    }
+                }
+            }
+            Real rho, v[3], p, cs;
+            if (!primitives<DIM>(u, gamma, rho, v, p, cs)) bad = 1;
+            const Real eps = av ? epsfac * clamp01(u[NC]) * cs : Real(0);
+            Real Gv = Real(1);
+            int jj[3] = {j % Q, (j / Q) % Q, j / (Q * Q)};
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) Gv *= tG[jj[a]];
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                Real F[NC];
+                euler_flux<DIM>(u, v, p, a, F);
+                if (ns) {
+                    Real Fn[NC];
+                    ns_flux<DIM>(u, gr, gamma, nu, kappa, a, Fn);
+#pragma unroll
+                    for (int f = 0; f < NC; ++f) F[f] -= Fn[f];
+                }
+                if (av) {
+#pragma unroll
+                    for (int f = 0; f < NC; ++f) F[f] -= eps * gr[a][f];
+                }
+                Real Gp = Real(1);
+#pragma unroll
+                for (int q = 0; q < DIM; ++q)
+                    if (q != a) Gp *= tG[jj[q]];
+                const Real w = cax[a] * Gp;
+#pragma unroll
+                for (int f = 0; f < NC; ++f) sW[((a * NC + f) * TC + c) * NP + j] = w * F[f];
+            }
+            if (av) {
+                Real div = Real(0);
+#pragma unroll
+                for (int a = 0; a < DIM; ++a) div += (gr[a][1 + a] - v[a] * gr[a][0]) / rho;
+                const Real adot = f_v * fmax(Real(0), -div) + sWig[c] - u[NC] * cs * inv_tau;
+                sR[(NC * TC + c) * NP + j] = src_w * Gv * adot;
+            }
+        }
+    }
+
+    // ---- faces: recovered interface state (needed for tangential derivatives)
+    auto decode_face = [&](int face, int &a, int &p, int *cc) -> bool {
+        a = face < S::FOFF(1) ? 0 : ((DIM == 2 || face < S::FOFF(2)) ? 1 : 2);
+        const int fl = face - S::FOFF(a);
+        p = fl % (S::T(a) + 1);
+        const int t = fl / (S::T(a) + 1);
+        cc[0] = cc[1] = cc[2] = 0;
+        S::untrans(a, t, cc);
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            if (q != a && cc[q] >= V[q]) return false;
+        return p <= V[a];
+    };
+    auto tile_slot = [&](const int *cc) { return cc[0] + TX * (cc[1] + TY * cc[2]); };
+
+    if (ns) {
+        for (int idx = tid; idx < NC * NFACE * NPF; idx += nth) {
+            const int k = idx % NPF;
+            const int fc = idx / NPF;
+            const int face = fc % NFACE, f = fc / NFACE;
+            int a, p, cc[3];
+            if (!decode_face(face, a, p, cc)) continue;
+            int cl[3] = {cc[0], cc[1], cc[2]}, cr[3] = {cc[0], cc[1], cc[2]};
+            cl[a] = p - 1;
+            cr[a] = p;
+            const int tt = S::trans(a, cc[0], cc[1], cc[2]);
+            const int sl = p > 0 ? tile_slot(cl) : S::HOFF(a, 0) + tt;
+            const int sr = p < V[a] ? tile_slot(cr) : S::HOFF(a, 1) + tt;
+            if (sG[sl] < 0 || sG[sr] < 0) continue;  // outflow boundary face
+            const int Sa = S::S(a);
+            const int base = S::knode(a, 0, k);
+            const Real *pl = sU + (f * NSLOT + sl) * NP + base;
+            const Real *pr = sU + (f * NSLOT + sr) * NP + base;
+            Real acc = Real(0);
+#pragma unroll
+            for (int m = 0; m < Q; ++m) acc = fma(tCm[m], pl[m * Sa], fma(tCp[m], pr[m * Sa], acc));
+            sUt[idx] = acc;
+        }
+    }
+    __syncthreads();
+
+    // ---- faces: HLLC + recovered dissipative flux, pre-weighted for the lift
+    {
+        const Real inv_f = Tg.inv_f;
+        for (int idx = tid; idx < NFACE * NPF; idx += nth) {
+            const int k = idx % NPF, face = idx / NPF;
+            int a, p, cc[3];
+            if (!decode_face(face, a, p, cc)) continue;
+            int cl[3] = {cc[0], cc[1], cc[2]}, cr[3] = {cc[0], cc[1], cc[2]};
+            cl[a] = p - 1;
+            cr[a] = p;
+            const int tt = S::trans(a, cc[0], cc[1], cc[2]);
+            const int sl = p > 0 ? tile_slot(cl) : S::HOFF(a, 0) + tt;
+            const int sr = p < V[a] ? tile_slot(cr) : S::HOFF(a, 1) + tt;
+            const int Sa = S::S(a);
+            const int base = S::knode(a, 0, k);
+            Real Fh[NC];
+            if (sG[sl] < 0 || sG[sr] < 0) {
+                // outflow boundary: physical flux of the interior trace
+                const bool right_in = sG[sl] < 0;
+                const int si = right_in ? sr : sl;
+                const Real *Lx = right_in ? tLm : tLp;
+                Real u[NC], v[3], rho, pr_, cs;
+#pragma unroll
+                for (int f = 0; f < NC; ++f) {
+                    const Real *q = sU + (f * NSLOT + si) * NP + base;
+                    Real acc = Real(0);
+#pragma unroll
+                    for (int m = 0; m < Q; ++m) acc = fma(Lx[m], q[m * Sa], acc);
+                    u[f] = acc;
+                }
+                if (!primitives<DIM>(u, gamma, rho, v, pr_, cs)) bad = 1;
+                euler_flux<DIM>(u, v, pr_, a, Fh);
+            } else {
+                Real uL[NC + 1], uR[NC + 1];
+                const int nfl = av ? NC + 1 : NC;
+                for (int f = 0; f < nfl; ++f) {
+                    const Real *ql = sU + (f * NSLOT + sl) * NP + base;
+                    const Real *qr = sU + (f * NSLOT + sr) * NP + base;
+                    Real al = Real(0), ar = Real(0);
+#pragma unroll
+                    for (int m = 0; m < Q; ++m) {
+                        al = fma(tLp[m], ql[m * Sa], al);
+                        ar = fma(tLm[m], qr[m * Sa], ar);
+                    }
+                    uL[f] = al;
+                    uR[f] = ar;
+                }
+                if (!hllc<DIM>(uL, uR, gamma, a, Fh)) bad = 1;
+                if (ns || av) {
+                    Real dn[NC];
+                    const Real sc = inv_f / (Real)A.h[a];
+#pragma unroll
+                    for (int f = 0; f < NC; ++f) {
+                        const Real *ql = sU + (f * NSLOT + sl) * NP + base;
+                        const Real *qr = sU + (f * NSLOT + sr) * NP + base;
+                        Real acc = Real(0);
+#pragma unroll
+                        for (int m = 0; m < Q; ++m) acc = fma(tDm[m], ql[m * Sa], fma(tDp[m], qr[m * Sa], acc));
+                        dn[f] = acc * sc;
+                    }
+                    if (ns) {
+                        Real ut[NC], grd[DIM][NC];
+                        const int k0 = k % Q, k1 = k / Q;
+#pragma unroll
+                        for (int f = 0; f < NC; ++f) {
+                            const Real *pf = sUt + (f * NFACE + face) * NPF;
+                            ut[f] = pf[k];
+                            grd[a][f] = dn[f];
+                            // transverse axes in increasing order; face strides 1 and Q
+                            int tb = 0;
+#pragma unroll
+                            for (int bb = 0; bb < DIM; ++bb) {
+                                if (bb == a) continue;
+                                const int kb = tb == 0 ? k0 : k1;
+                                const int sb = tb == 0 ? 1 : Q;
+                                const Real *q = pf + (k - kb * sb);
+                                Real acc = Real(0);
+#pragma unroll
+                                for (int m = 0; m < Q; ++m) acc = fma(tDn[kb * Q + m], q[m * sb], acc);
+                                grd[bb][f] = acc * two_h[bb];
+                                ++tb;
+                            }
+                        }
+                        if (!(ut[0] > Real(0))) bad = 1;
+                        Real Fn[NC];
+                        ns_flux<DIM>(ut, grd, gamma, nu, kappa, a, Fn);
+#pragma unroll
+                        for (int f = 0; f < NC; ++f) Fh[f] -= Fn[f];
+                    }
+                    if (av) {
+                        Real r1, v1[3], p1, c1, r2, v2[3], p2, c2;
+                        primitives<DIM>(uL, gamma, r1, v1, p1, c1);
+                        primitives<DIM>(uR, gamma, r2, v2, p2, c2);
+                        const Real eps = Real(0.5) * epsfac * (clamp01(uL[NC]) * c1 + clamp01(uR[NC]) * c2);
+#pragma unroll
+                        for (int f = 0; f < NC; ++f) Fh[f] -= eps * dn[f];
+                    }
+                }
+            }
+            Real Gp = tG[k % Q];
+            if (DIM == 3) Gp *= tG[k / Q];
+            const Real w = cax[a] * Gp;
+#pragma unroll
+            for (int f = 0; f < NC; ++f) sFh[(f * NFACE + face) * NPF + k] = w * Fh[f];
+        }
+    }
+    __syncthreads();
+
+    // ---- nodal residual: weak divergence of the volume flux + lift of the face fluxes
+    {
+        for (int idx = tid; idx < NC * TC * NP; idx += nth) {
+            const int n = idx % NP;
+            const int fc = idx / NP;
+            const int c = fc % TC, f = fc / TC;
+            if (sG[c] < 0) continue;
+            const int cc[3] = {c % TX, (c / TX) % TY, c / (TX * TY)};
+            Real r = Real(0);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                const int Sa = S::S(a);
+                const int i = (n / Sa) % Q;
+                const Real *Fp = sW + ((a * NC + f) * TC + c) * NP + (n - i * Sa);
+#pragma unroll
+                for (int m = 0; m < Q; ++m) r = fma(tWd[i * Q + m], Fp[m * Sa], r);
+                const int tt = S::trans(a, cc[0], cc[1], cc[2]);
+                const int fl = S::FOFF(a) + cc[a] + (S::T(a) + 1) * tt;
+                const int k = S::ktrans(a, n);
+                const Real FL = sFh[(f * NFACE + fl) * NPF + k];
+                const Real FR = sFh[(f * NFACE + fl + 1) * NPF + k];
+                r = fma(tLm[i], FL, r);
+                r = fma(-tLp[i], FR, r);
+            }
+            sR[idx] = r;
+        }
+    }
+    __syncthreads();
+
+    // ---- nodal -> modal (transposed passes) over all fields
+    Real *res;
+    {
+        Real *src = sR, *dst = sW;
+        const int total = nf * TC * NP;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            const int Sa = S::S(a);
+            for (int idx = tid; idx < total; idx += nth) {
+                const int l = idx % NP;
+                const int fc = idx / NP;
+                if (sG[fc % TC] < 0) continue;
+                const int la = (l / Sa) % Q;
+                const Real *p = src + fc * NP + (l - la * Sa);
+                Real acc = Real(0);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) acc = fma(tB[i * Q + la], p[i * Sa], acc);
+                dst[idx] = acc;
+            }
+            Real *t = src;
+            src = dst;
+            dst = t;
+            __syncthreads();
+        }
+        res = src;
+    }
+
+    // ---- epilogue: write L or apply the Runge-Kutta stage (delta form)
+    {
+        const int total = nf * TC * NP;
+        const Real dt = A.dtp ? (Real)A.dtp[0] : Real(0);
+        const Real ca = (Real)A.ca, cx = (Real)A.cx, cb = (Real)A.cb;
+        const Real za = (Real)A.za, zx = (Real)A.zx, zb = (Real)A.zb;
+        const Real *di = static_cast<const Real *>(A.din);
+        Real *xb = static_cast<Real *>(A.xbuf);
+        Real *dout = static_cast<Real *>(A.dout);
+        const bool readx = xb && (A.cx != 0.0 || A.zx != 0.0);
+        for (int idx = tid; idx < total; idx += nth) {
+            const int l = idx % NP;
+            const int fc = idx / NP;
+            const int c = fc % TC, f = fc / TC;
+            const int g = sG[c];
+            if (g < 0) continue;
+            const Real L = res[idx];
+            const size_t gi = ((size_t)f * A.ncell + g) * NP + l;
+            if (A.mode == 0) {
+                A.rhs_out[gi] = (double)L;
+                continue;
+            }
+            const Real dtL = dt * L;
+            const Real din = di ? di[gi] : Real(0);
+            const Real x = readx ? xb[gi] : Real(0);
+            const Real dnew = ca * din + cx * x + cb * dtL;
+            if (A.write_z) xb[gi] = za * din + zx * x + zb * dtL;
+            if (A.mode == 1) {
+                dout[gi] = dnew;
+            } else {
+                const double un = A.uold[gi] + (double)dnew;
+                A.unew[gi] = un;
+                if (A.uhi_new) A.uhi_new[gi] = (float)un;
+            }
+        }
+    }
+    if (bad) s_status = 1;
+    __syncthreads();
+    if (tid == 0 && s_status) atomicOr(A.status, DG_STATUS_NONPHYS);
+}
+
+// ------------------------------------------------------------------ step prologue: sensor + CFL speeds
+
+template <int DIM, int N, typename Real, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(256) prologue_kernel(const PrologueArgs A, const Tables<Real> Tg)
+{
+    using S = Shape<DIM, N, TX, TY, TZ>;
+    using PL = ProloguePlan<DIM, N, Real, TX, TY, TZ>;
+    constexpr int Q = S::Q, NP = S::NP, NC = S::NC, TC = S::TC;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real *sm = reinterpret_cast<Real *>(smem_raw);
+    Real *tB = sm;
+    Real *sU = sm + PL::TAB, *sW = sU + PL::SZ;
+    int *sG = reinterpret_cast<int *>(sm + PL::NREAL);
+    __shared__ double red[2][32];
+    __shared__ int s_bad;
+
+    const int tid = threadIdx.x, nth = blockDim.x;
+    int b = blockIdx.x;
+    const int tx = b % A.ntile[0];
+    b /= A.ntile[0];
+    const int ty = b % A.ntile[1];
+    const int tz = b / A.ntile[1];
+    const int o[3] = {tx * TX, ty * TY, tz * TZ};
+    const int V[3] = {min(TX, A.N[0] - o[0]), min(TY, A.N[1] - o[1]), DIM == 3 ? min(TZ, A.N[2] - o[2]) : 1};
+    for (int i = tid; i < Q * Q; i += nth) tB[i] = Tg.B[i / Q][i % Q];
+    for (int c = tid; c < TC; c += nth) {
+        const int cc[3] = {c % TX, (c / TX) % TY, c / (TX * TY)};
+        sG[c] = (cc[0] < V[0] && cc[1] < V[1] && cc[2] < V[2])
+                    ? (o[0] + cc[0]) + A.N[0] * ((o[1] + cc[1]) + A.N[1] * (o[2] + cc[2]))
+                    : -1;
+    }
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    const Real *u = static_cast<const Real *>(A.u);
+    for (int idx = tid; idx < NC * TC * NP; idx += nth) {
+        const int l = idx % NP, fc = idx / NP;
+        const int c = fc % TC, f = fc / TC;
+        const int g = sG[c];
+        sU[idx] = g >= 0 ? u[((size_t)f * A.ncell + g) * NP + l] : Real(0);
+    }
+    __syncthreads();
+    if (A.update_sensor) {
+        const double dt_prev = A.dtp[0];
+        const double step = A.dtp[1];
+        for (int c = tid; c < TC; c += nth) {
+            const int g = sG[c];
+            if (g < 0) continue;
+            Real hi = Real(0), all = Real(0);
+            for (int l = 0; l < NP; ++l) {
+                const Real w = sU[c * NP + l];  // density field (f = 0)
+                const int l0 = l % Q, l1 = (l / Q) % Q, l2 = DIM == 3 ? l / (Q * Q) : 0;
+                const bool top = N > 0 && (l0 == N || l1 == N || (DIM == 3 && l2 == N));
+                all += w * w;
+                if (top) hi += w * w;
+            }
+            const double Sk = all > Real(0) ? (double)(hi / all) : 0.0;
+            double dlog = 0.0;
+            // S is floored four decades below the onset threshold: below that its value is rounding
+            // noise of the higher modes, and a log of noise would turn into a source of size noise / dt
+            const double s_floor = 1e-4 * A.s_on;
+            if (step > 0.0 && dt_prev > 0.0)
+                dlog = (log(fmax(Sk, s_floor)) - log(fmax(A.S_prev[g], s_floor))) / dt_prev;
+            A.wig[g] = (Sk > A.s_on) ? A.f_w * fmax(0.0, dlog) : 0.0;
+            A.S_prev[g] = Sk;
+        }
+    }
+    // modal -> nodal for the conserved fields
+    Real *src = sU, *dst = sW;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        const int Sa = S::S(a);
+        for (int idx = tid; idx < NC * TC * NP; idx += nth) {
+            const int j = idx % NP, fc = idx / NP;
+            if (sG[fc % TC] < 0) continue;
+            const int i = (j / Sa) % Q;
+            const Real *p = src + fc * NP + (j - i * Sa);
+            Real acc = Real(0);
+#pragma unroll
+            for (int m = 0; m < Q; ++m) acc = fma(tB[i * Q + m], p[m * Sa], acc);
+            dst[idx] = acc;
+        }
+        Real *t = src;
+        src = dst;
+        dst = t;
+        __syncthreads();
+    }
+    double cmax = 0.0, vmax = 0.0;
+    int bad = 0;
+    const Real gamma = (Real)A.gamma;
+    for (int idx = tid; idx < TC * NP; idx += nth) {
+        const int c = idx / NP, j = idx % NP;
+        if (sG[c] < 0) continue;
+        Real uu[NC];
+#pragma unroll
+        for (int f = 0; f < NC; ++f) uu[f] = src[(f * TC + c) * NP + j];
+        Real rho, v[3], p, cs;
+        if (!primitives<DIM>(uu, gamma, rho, v, p, cs)) bad = 1;
+        Real v2 = Real(0);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) v2 += v[a] * v[a];
+        cmax = fmax(cmax, (double)cs);
+        vmax = fmax(vmax, (double)sqrt(v2));
+    }
+    // block max-reduction: warp shuffle, then one value per warp
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, off));
+        vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, off));
+    }
+    const int warp = tid >> 5, lane = tid & 31;
+    if (lane == 0) {
+        red[0][warp] = cmax;
+        red[1][warp] = vmax;
+    }
+    if (bad) s_bad = 1;
+    __syncthreads();
+    if (tid == 0) {
+        double c0 = 0.0, v0 = 0.0;
+        for (int w = 0; w < (nth + 31) / 32; ++w) {
+            c0 = fmax(c0, red[0][w]);
+            v0 = fmax(v0, red[1][w]);
+        }
+        A.partial[2 * blockIdx.x + 0] = c0;
+        A.partial[2 * blockIdx.x + 1] = v0;
+        if (s_bad) atomicOr(A.status, DG_STATUS_NONPHYS);
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+
+template <int DIM, int N, typename Real, int TX, int TY, int TZ>
+cudaError_t run_stage(const StageArgs &a, const Tables<Real> &t, cudaStream_t s)
+{
+    using PL = StagePlan<DIM, N, Real, TX, TY, TZ>;
+    auto k = stage_kernel<DIM, N, Real, TX, TY, TZ>;
+    static_assert(PL::BYTES <= 227 * 1024, "stage tile exceeds shared memory");
+    static bool attr_set = false;  // first call comes from the handle set-up, never from a graph capture
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int blocks = a.ntile[0] * a.ntile[1] * a.ntile[2];
+    if (blocks == 0) return cudaSuccess;  // attribute set-up only (done before any graph capture)
+    k<<<blocks, 256, PL::BYTES, s>>>(a, t);
+    return cudaGetLastError();
+}
+
+template <int DIM, int N, typename Real, int TX, int TY, int TZ>
+cudaError_t run_prologue(const PrologueArgs &a, const Tables<Real> &t, cudaStream_t s)
+{
+    using PL = ProloguePlan<DIM, N, Real, TX, TY, TZ>;
+    auto k = prologue_kernel<DIM, N, Real, TX, TY, TZ>;
+    static_assert(PL::BYTES <= 227 * 1024, "prologue tile exceeds shared memory");
+    static bool attr_set = false;  // first call comes from the handle set-up, never from a graph capture
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int blocks = a.ntile[0] * a.ntile[1] * a.ntile[2];
+    if (blocks == 0) return cudaSuccess;
+    k<<<blocks, 256, PL::BYTES, s>>>(a, t);
+    return cudaGetLastError();
+}
+
+}  // namespace dgx
