@@ -155,6 +155,31 @@ int dg_conserved_sums(dg_t *h, double *out);
 int dg_get_aux(dg_t *h, double *S_prev, double *wig, double *scal);
 int dg_set_aux(dg_t *h, const double *S_prev, const double *wig, const double *scal);
 
+/* The CFL time step of Eq. timestep, like dg_max_dt, for callers that cannot
+ * let a library allocate device memory: code that hands all device memory to
+ * its own pool at start-up and forbids later allocations, or time-stepping
+ * loops that cannot take the device synchronisation of cudaMalloc/cudaFree.
+ * The paper has no counterpart; this is a service of this library.
+ *
+ * Needs no handle and allocates nothing.  dev_state: device pointer to the
+ * FP64 state in the layout above (its first d+2 fields are read; an alpha
+ * field may follow).  dev_dt: device pointer to one double that receives the
+ * step, or NaN if a Gauss point has rho <= 0 or p <= 0.  grid->bc is unused.
+ * Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default stream)
+ * without a host synchronisation; the arithmetic is that of dg_max_dt in FP64.
+ *
+ * Scratch: a 4 MiB file-scope device array (2^18 per-tile slots + a status
+ * word) that every GPU which loads the library keeps until the process exits.
+ * Grids that need more than 2^18 tiles of the time-step kernel (e.g. more than
+ * 4.19 M cells in 3-D at degree 3, 16.7 M cells in 2-D at degree 3) return
+ * DG_EUNSUPPORTED.  All calls share that array: calls whose work overlaps on
+ * the GPU (different streams, or different host threads) race and must be
+ * serialised by the caller.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  Returns DG_OK, DG_EINVAL, DG_EUNSUPPORTED or DG_ECUDA. */
+int dg_max_dt_noalloc(const dg_grid *grid, int degree, double gamma, double cfl, const double *dev_state,
+                      double *dev_dt, void *stream);
+
 const char *dg_last_error(const dg_t *h);
 const char *dg_status_string(int code);
 

@@ -27,7 +27,7 @@ EXPORTS = (
     "dg_default_params", "dg_create", "dg_destroy", "dg_set_params", "dg_get_params", "dg_sizes",
     "dg_set_stream", "dg_set_state", "dg_get_state", "dg_set_state_device", "dg_get_state_device",
     "dg_rhs", "dg_rhs_device", "dg_step", "dg_steps", "dg_step_timed", "dg_sync", "dg_max_dt", "dg_conserved_sums",
-    "dg_get_aux", "dg_set_aux", "dg_last_error", "dg_status_string",
+    "dg_get_aux", "dg_set_aux", "dg_last_error", "dg_status_string", "dg_max_dt_noalloc",
 )
 
 
@@ -80,6 +80,8 @@ def lib(path: str = LIB_PATH):
         "dg_sync": (I, [H]), "dg_max_dt": (I, [H, P]), "dg_conserved_sums": (I, [H, P]),
         "dg_get_aux": (I, [H, P, P, P]), "dg_set_aux": (I, [H, P, P, P]),
         "dg_last_error": (ctypes.c_char_p, [H]), "dg_status_string": (ctypes.c_char_p, [I]),
+        "dg_max_dt_noalloc": (I, [ctypes.POINTER(dg_grid), I, ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -207,6 +209,15 @@ def dg_set_aux(h, S_prev=None, wig=None, scal=None):
     cv = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)
     S_prev, wig, scal = cv(S_prev), cv(wig), cv(scal)
     _check(h, lib().dg_set_aux(h, _dp(S_prev), _dp(wig), _dp(scal)))
+
+
+def dg_max_dt_noalloc(grid: dg_grid, degree: int, gamma: float, cfl: float, dev_state_ptr: int, dev_dt_ptr: int,
+                      stream_ptr: int = 0):
+    """CFL step into a caller-owned device double; allocates nothing (see include/dgx.h)."""
+    code = lib().dg_max_dt_noalloc(ctypes.byref(grid), int(degree), float(gamma), float(cfl),
+                                   ctypes.c_void_p(dev_state_ptr), ctypes.c_void_p(dev_dt_ptr),
+                                   ctypes.c_void_p(stream_ptr))
+    _check(None, code)
 
 
 # ---------------------------------------------------------------- convenience wrapper
