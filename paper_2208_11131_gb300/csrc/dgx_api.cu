@@ -356,7 +356,8 @@ cudaError_t launch_prologue_any(const dg_t *h, int update_sensor)
 int prepare_kernels(dg_t *h)
 {
     StageArgs a;
-    memset(&a, 0, sizeof a);
+    base_stage_args(h, a);
+    a.ntile[0] = a.ntile[1] = a.ntile[2] = 0;
     CK(h, launch_stage_any(h, a));
     PrologueArgs pa;
     memset(&pa, 0, sizeof pa);

@@ -2,7 +2,11 @@
 // (dimension, precision) pair.  The including unit defines
 //   DGX_DIM, DGX_REAL, DGX_SUFFIX and DGX_TILES(X) with one
 //   X(degree, stage TX,TY,TZ, prologue TX,TY,TZ) entry per degree 0..5.
-#include "dgx_kernels.cuh"
+#include "dgx_stage2.cuh"
+
+// DGX_STAGE_RUN selects the stage kernel of the unit: run_stage2_any (persistent, prefetching,
+// line-oriented; 2-D) or run_stage (tile-per-CTA; 3-D, whose tiles do not leave room for the
+// prefetch buffers)
 
 #define DGX_CAT2(a, b) a##b
 #define DGX_CAT(a, b) DGX_CAT2(a, b)
@@ -11,7 +15,7 @@ namespace dgx {
 
 #define DGX_STAGE_CASE(n, sx, sy, sz, px, py, pz) \
     case n:                                       \
-        return run_stage<DGX_DIM, n, DGX_REAL, sx, sy, sz>(a, t, s);
+        return DGX_STAGE_RUN<DGX_DIM, n, DGX_REAL, sx, sy, sz>(a, t, s);
 #define DGX_PRO_CASE(n, sx, sy, sz, px, py, pz) \
     case n:                                     \
         return run_prologue<DGX_DIM, n, DGX_REAL, px, py, pz>(a, t, s);

@@ -1,5 +1,6 @@
-// Device code of the modal DG right-hand side and SSP-RK stage update
-// (arXiv 2208.11131, Sec. 2-4), written for sm_103a.
+// Shared device code of the modal DG hot path (arXiv 2208.11131, Sec. 2-4) for sm_103a:
+// tile geometry, pointwise physics, and the step-prologue kernel.  The fused stage kernel
+// that uses them is in dgx_stage2.cuh.
 //
 // Formulation.  Each CTA owns a tile of cells plus the face-neighbour halo.
 // The stage state is loaded once into shared memory and turned from modal
@@ -109,49 +110,70 @@ __device__ __forceinline__ bool primitives(const Real *u, Real gamma, Real &rho,
     return ok;
 }
 
+// Euler flux along axis a (a may be a run-time value: selected by value, no run-time indexing)
 template <int DIM, typename Real>
 __device__ __forceinline__ void euler_flux(const Real *u, const Real *v, Real p, int a, Real *F)
 {
-    const Real va = v[a];
-    F[0] = u[1 + a];
+    Real va = v[0], ma = u[1];
+#pragma unroll
+    for (int b = 1; b < DIM; ++b) {
+        va = b == a ? v[b] : va;
+        ma = b == a ? u[1 + b] : ma;
+    }
+    F[0] = ma;
 #pragma unroll
     for (int b = 0; b < DIM; ++b) F[1 + b] = u[1 + b] * va + (b == a ? p : Real(0));
     F[DIM + 1] = (u[DIM + 1] + p) * va;
 }
 
 // HLLC with Davis wave speeds (Toro); passive transverse momentum.  Returns false on a bad state.
+// Written without pointers to local arrays and without early returns: the side values that enter
+// the star state are chosen by value selects, so every array stays in registers.
 template <int DIM, typename Real>
 __device__ __forceinline__ bool hllc(const Real *uL, const Real *uR, Real gamma, int a, Real *F)
 {
     Real rL, rR, pL, pR, cL, cR, vL[3], vR[3];
     bool ok = primitives<DIM>(uL, gamma, rL, vL, pL, cL);
     ok = primitives<DIM>(uR, gamma, rR, vR, pR, cR) && ok;
-    const Real SL = fmin(vL[a] - cL, vR[a] - cR);
-    const Real SR = fmax(vL[a] + cL, vR[a] + cR);
-    if (SL >= Real(0)) {
-        euler_flux<DIM>(uL, vL, pL, a, F);
-        return ok;
+    Real vnL = vL[0], vnR = vR[0];
+#pragma unroll
+    for (int b = 1; b < DIM; ++b) {
+        vnL = b == a ? vL[b] : vnL;
+        vnR = b == a ? vR[b] : vnR;
     }
-    if (SR < Real(0)) {
-        euler_flux<DIM>(uR, vR, pR, a, F);
-        return ok;
-    }
-    const Real num = pR - pL + rL * vL[a] * (SL - vL[a]) - rR * vR[a] * (SR - vR[a]);
-    const Real den = rL * (SL - vL[a]) - rR * (SR - vR[a]);
+    const Real SL = fmin(vnL - cL, vnR - cR);
+    const Real SR = fmax(vnL + cL, vnR + cR);
+    const Real num = pR - pL + rL * vnL * (SL - vnL) - rR * vnR * (SR - vnR);
+    const Real den = rL * (SL - vnL) - rR * (SR - vnR);
     const Real Ss = num / den;
-    const bool left = Ss >= Real(0);
-    const Real *uK = left ? uL : uR;
-    const Real *vK = left ? vL : vR;
-    const Real rK = left ? rL : rR, pK = left ? pL : pR, SK = left ? SL : SR;
-    euler_flux<DIM>(uK, vK, pK, a, F);
-    const Real fac = rK * (SK - vK[a]) / (SK - Ss);
-    Real us[DIM + 2];
-    us[0] = fac;
+    // region: 0 = left state, 1 = left star, 2 = right star, 3 = right state
+    const int region = SL >= Real(0) ? 0 : (Ss >= Real(0) ? 1 : (SR >= Real(0) ? 2 : 3));
+    const bool left = region <= 1;
+    Real uK[DIM + 2], vK[DIM];
 #pragma unroll
-    for (int b = 0; b < DIM; ++b) us[1 + b] = fac * (b == a ? Ss : vK[b]);
-    us[DIM + 1] = fac * (uK[DIM + 1] / rK + (Ss - vK[a]) * (Ss + pK / (rK * (SK - vK[a]))));
+    for (int f = 0; f < DIM + 2; ++f) uK[f] = left ? uL[f] : uR[f];
 #pragma unroll
-    for (int f = 0; f < DIM + 2; ++f) F[f] += SK * (us[f] - uK[f]);
+    for (int b = 0; b < DIM; ++b) vK[b] = left ? vL[b] : vR[b];
+    const Real rK = left ? rL : rR, pK = left ? pL : pR, vnK = left ? vnL : vnR;
+    const Real SK = left ? SL : SR;
+    // physical flux of the chosen side
+    Real mK = uK[1];
+#pragma unroll
+    for (int b = 1; b < DIM; ++b) mK = b == a ? uK[1 + b] : mK;
+    F[0] = mK;
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) F[1 + b] = uK[1 + b] * vnK + (b == a ? pK : Real(0));
+    F[DIM + 1] = (uK[DIM + 1] + pK) * vnK;
+    if (region == 1 || region == 2) {
+        const Real fac = rK * (SK - vnK) / (SK - Ss);
+        Real us[DIM + 2];
+        us[0] = fac;
+#pragma unroll
+        for (int b = 0; b < DIM; ++b) us[1 + b] = fac * (b == a ? Ss : vK[b]);
+        us[DIM + 1] = fac * (uK[DIM + 1] / rK + (Ss - vnK) * (Ss + pK / (rK * (SK - vnK))));
+#pragma unroll
+        for (int f = 0; f < DIM + 2; ++f) F[f] += SK * (us[f] - uK[f]);
+    }
     return ok;
 }
 
@@ -189,26 +211,6 @@ __device__ __forceinline__ void ns_flux(const Real *u, const Real (*grad)[DIM + 
 }
 
 // ------------------------------------------------------------------ shared memory plan
-
-template <int DIM, int N, typename Real, int TX, int TY, int TZ>
-struct StagePlan {
-    using S = Shape<DIM, N, TX, TY, TZ>;
-    static constexpr int Q = S::Q;
-    static constexpr int TAB = 3 * Q * Q + 7 * Q + 1;
-    static constexpr int SZ_U = S::NFM * S::NSLOT * S::NP;
-    static constexpr int SZ_F = DIM * S::NC * S::TC * S::NP;
-    static constexpr int SZ_W = SZ_U > SZ_F ? SZ_U : SZ_F;
-    static constexpr int SZ_R = S::NFM * S::TC * S::NP;
-    static constexpr int SZ_FACE = S::NC * S::NFACE * S::NPF;
-    static constexpr int OFF_U = (TAB + 3) / 4 * 4;
-    static constexpr int OFF_W = OFF_U + SZ_U;
-    static constexpr int OFF_R = OFF_W + SZ_W;
-    static constexpr int OFF_UT = OFF_R + SZ_R;
-    static constexpr int OFF_FH = OFF_UT + SZ_FACE;
-    static constexpr int OFF_WIG = OFF_FH + SZ_FACE;
-    static constexpr int NREAL = OFF_WIG + (S::TC + 3) / 4 * 4;
-    static constexpr size_t BYTES = sizeof(Real) * (size_t)NREAL + sizeof(int) * (size_t)S::NSLOT;
-};
 
 template <int DIM, int N, typename Real, int TX, int TY, int TZ>
 struct ProloguePlan {
@@ -262,433 +264,6 @@ __device__ __forceinline__ int slot_global(int slot, const int *o, const int *V,
     }
     g[a] = ca;
     return g[0] + N[0] * (g[1] + N[1] * g[2]);
-}
-
-// ------------------------------------------------------------------ the fused stage kernel
-
-template <int DIM, int N, typename Real, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(256) stage_kernel(const StageArgs A, const Tables<Real> Tg)
-{
-    using S = Shape<DIM, N, TX, TY, TZ>;
-    using PL = StagePlan<DIM, N, Real, TX, TY, TZ>;
-    constexpr int Q = S::Q, NP = S::NP, NPF = S::NPF, NC = S::NC, TC = S::TC, NSLOT = S::NSLOT;
-    constexpr int NFACE = S::NFACE;
-
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Real *sm = reinterpret_cast<Real *>(smem_raw);
-    Real *tB = sm, *tDn = tB + Q * Q, *tWd = tDn + Q * Q, *tG = tWd + Q * Q;
-    Real *tLp = tG + Q, *tLm = tLp + Q, *tCm = tLm + Q, *tCp = tCm + Q, *tDm = tCp + Q, *tDp = tDm + Q;
-    Real *sU = sm + PL::OFF_U, *sW = sm + PL::OFF_W, *sR = sm + PL::OFF_R;
-    Real *sUt = sm + PL::OFF_UT, *sFh = sm + PL::OFF_FH, *sWig = sm + PL::OFF_WIG;
-    int *sG = reinterpret_cast<int *>(sm + PL::NREAL);
-    __shared__ int s_status;
-
-    const int tid = threadIdx.x, nth = blockDim.x;
-    const int nf = A.nf;
-    const bool av = A.av_on != 0, ns = A.ns_on != 0;
-    const bool need_grad = av || ns;
-
-    int b = blockIdx.x;
-    const int tx = b % A.ntile[0];
-    b /= A.ntile[0];
-    const int ty = b % A.ntile[1];
-    const int tz = b / A.ntile[1];
-    const int o[3] = {tx * TX, ty * TY, tz * TZ};
-    const int V[3] = {min(TX, A.N[0] - o[0]), min(TY, A.N[1] - o[1]), DIM == 3 ? min(TZ, A.N[2] - o[2]) : 1};
-
-    for (int i = tid; i < Q * Q; i += nth) {
-        tB[i] = Tg.B[i / Q][i % Q];
-        tDn[i] = Tg.Dn[i / Q][i % Q];
-        tWd[i] = Tg.Wd[i / Q][i % Q];
-    }
-    for (int i = tid; i < Q; i += nth) {
-        tG[i] = Tg.G[i];
-        tLp[i] = Tg.Lp[i];
-        tLm[i] = Tg.Lm[i];
-        tCm[i] = Tg.Cm[i];
-        tCp[i] = Tg.Cp[i];
-        tDm[i] = Tg.Dm[i];
-        tDp[i] = Tg.Dp[i];
-    }
-    for (int s = tid; s < NSLOT; s += nth) sG[s] = slot_global<S>(s, o, V, A.N, A.bc);
-    if (tid == 0) s_status = 0;
-    __syncthreads();
-
-    // ---- load the stage state (u^n [+ delta]) of tile and halo cells
-    {
-        const Real *ub = static_cast<const Real *>(A.ubase);
-        const Real *di = static_cast<const Real *>(A.din);
-        const int total = nf * NSLOT * NP;
-        for (int idx = tid; idx < total; idx += nth) {
-            const int l = idx % NP;
-            const int fs = idx / NP;
-            const int slot = fs % NSLOT, f = fs / NSLOT;
-            const int g = sG[slot];
-            Real v = Real(0);
-            if (g >= 0) {
-                const size_t gi = ((size_t)f * A.ncell + g) * NP + l;
-                v = ub[gi];
-                if (di) v += di[gi];
-            }
-            sU[idx] = v;
-        }
-        for (int c = tid; c < TC; c += nth) sWig[c] = (av && sG[c] >= 0) ? (Real)A.wig[sG[c]] : Real(0);
-    }
-    __syncthreads();
-
-    // ---- modal -> nodal, d sum-factorised passes over all fields and slots
-    {
-        Real *src = sU, *dst = sW;
-        const int total = nf * NSLOT * NP;
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) {
-            const int Sa = S::S(a);
-            for (int idx = tid; idx < total; idx += nth) {
-                const int j = idx % NP;
-                const int fs = idx / NP;
-                if (sG[fs % NSLOT] < 0) continue;
-                const int i = (j / Sa) % Q;
-                const Real *p = src + fs * NP + (j - i * Sa);
-                Real acc = Real(0);
-#pragma unroll
-                for (int m = 0; m < Q; ++m) acc = fma(tB[i * Q + m], p[m * Sa], acc);
-                dst[idx] = acc;
-            }
-            Real *t = src;
-            src = dst;
-            dst = t;
-            __syncthreads();
-        }
-        if (DIM == 3) {  // result landed in sW: move it back to sU
-            for (int idx = tid; idx < total; idx += nth) sU[idx] = sW[idx];
-            __syncthreads();
-        }
-    }
-
-    const Real gamma = (Real)A.gamma, nu = (Real)A.nu, kappa = (Real)A.kappa;
-    const Real P = (Real)(N + 1);
-    const Real epsfac = (Real)(A.av_scale * A.hmin / (N + 1));
-    const Real inv_tau = (Real)((N + 1) / (A.f_tau * A.hmin));  // times c_s
-    const Real f_v = (Real)A.f_v;
-    Real two_h[3], cax[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        two_h[a] = (Real)(2.0 / A.h[a]);
-        cax[a] = (Real)((DIM == 2 ? 0.5 : 0.25) / A.h[a]);
-    }
-    const Real src_w = (Real)(DIM == 2 ? 0.25 : 0.125);
-    (void)P;
-    int bad = 0;
-
-    // ---- pointwise volume fluxes (Euler - NS - AV) and the alpha source
-    {
-        for (int idx = tid; idx < TC * NP; idx += nth) {
-            const int c = idx / NP, j = idx % NP;
-            if (sG[c] < 0) continue;
-            Real u[NC + 1];
-#pragma unroll
-            for (int f = 0; f < NC; ++f) u[f] = sU[(f * NSLOT + c) * NP + j];
-            u[NC] = av ? sU[(NC * NSLOT + c) * NP + j] : Real(0);
-            Real gr[DIM][NC];
-            if (need_grad) {
-#pragma unroll
-                for (int a = 0; a < DIM; ++a) {
-                    const int Sa = S::S(a);
-                    const int i = (j / Sa) % Q;
-                    const int base = j - i * Sa;
-#pragma unroll
-                    for (int f = 0; f < NC; ++f) {
-                        const Real *p = sU + (f * NSLOT + c) * NP + base;
-                        Real acc = Real(0);
-#pragma unroll
-                        for (int m = 0; m < Q; ++m) acc = fma(tDn[i * Q + m], p[m * Sa], acc);
-                        gr[a][f] = acc * two_h[a];
-                    }
-                }
-            }
-            Real rho, v[3], p, cs;
-            if (!primitives<DIM>(u, gamma, rho, v, p, cs)) bad = 1;
-            const Real eps = av ? epsfac * clamp01(u[NC]) * cs : Real(0);
-            Real Gv = Real(1);
-            int jj[3] = {j % Q, (j / Q) % Q, j / (Q * Q)};
-#pragma unroll
-            for (int a = 0; a < DIM; ++a) Gv *= tG[jj[a]];
-#pragma unroll
-            for (int a = 0; a < DIM; ++a) {
-                Real F[NC];
-                euler_flux<DIM>(u, v, p, a, F);
-                if (ns) {
-                    Real Fn[NC];
-                    ns_flux<DIM>(u, gr, gamma, nu, kappa, a, Fn);
-#pragma unroll
-                    for (int f = 0; f < NC; ++f) F[f] -= Fn[f];
-                }
-                if (av) {
-#pragma unroll
-                    for (int f = 0; f < NC; ++f) F[f] -= eps * gr[a][f];
-                }
-                Real Gp = Real(1);
-#pragma unroll
-                for (int q = 0; q < DIM; ++q)
-                    if (q != a) Gp *= tG[jj[q]];
-                const Real w = cax[a] * Gp;
-#pragma unroll
-                for (int f = 0; f < NC; ++f) sW[((a * NC + f) * TC + c) * NP + j] = w * F[f];
-            }
-            if (av) {
-                Real div = Real(0);
-#pragma unroll
-                for (int a = 0; a < DIM; ++a) div += (gr[a][1 + a] - v[a] * gr[a][0]) / rho;
-                const Real adot = f_v * fmax(Real(0), -div) + sWig[c] - u[NC] * cs * inv_tau;
-                sR[(NC * TC + c) * NP + j] = src_w * Gv * adot;
-            }
-        }
-    }
-
-    // ---- faces: recovered interface state (needed for tangential derivatives)
-    auto decode_face = [&](int face, int &a, int &p, int *cc) -> bool {
-        a = face < S::FOFF(1) ? 0 : ((DIM == 2 || face < S::FOFF(2)) ? 1 : 2);
-        const int fl = face - S::FOFF(a);
-        p = fl % (S::T(a) + 1);
-        const int t = fl / (S::T(a) + 1);
-        cc[0] = cc[1] = cc[2] = 0;
-        S::untrans(a, t, cc);
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-            if (q != a && cc[q] >= V[q]) return false;
-        return p <= V[a];
-    };
-    auto tile_slot = [&](const int *cc) { return cc[0] + TX * (cc[1] + TY * cc[2]); };
-
-    if (ns) {
-        for (int idx = tid; idx < NC * NFACE * NPF; idx += nth) {
-            const int k = idx % NPF;
-            const int fc = idx / NPF;
-            const int face = fc % NFACE, f = fc / NFACE;
-            int a, p, cc[3];
-            if (!decode_face(face, a, p, cc)) continue;
-            int cl[3] = {cc[0], cc[1], cc[2]}, cr[3] = {cc[0], cc[1], cc[2]};
-            cl[a] = p - 1;
-            cr[a] = p;
-            const int tt = S::trans(a, cc[0], cc[1], cc[2]);
-            const int sl = p > 0 ? tile_slot(cl) : S::HOFF(a, 0) + tt;
-            const int sr = p < V[a] ? tile_slot(cr) : S::HOFF(a, 1) + tt;
-            if (sG[sl] < 0 || sG[sr] < 0) continue;  // outflow boundary face
-            const int Sa = S::S(a);
-            const int base = S::knode(a, 0, k);
-            const Real *pl = sU + (f * NSLOT + sl) * NP + base;
-            const Real *pr = sU + (f * NSLOT + sr) * NP + base;
-            Real acc = Real(0);
-#pragma unroll
-            for (int m = 0; m < Q; ++m) acc = fma(tCm[m], pl[m * Sa], fma(tCp[m], pr[m * Sa], acc));
-            sUt[idx] = acc;
-        }
-    }
-    __syncthreads();
-
-    // ---- faces: HLLC + recovered dissipative flux, pre-weighted for the lift
-    {
-        const Real inv_f = Tg.inv_f;
-        for (int idx = tid; idx < NFACE * NPF; idx += nth) {
-            const int k = idx % NPF, face = idx / NPF;
-            int a, p, cc[3];
-            if (!decode_face(face, a, p, cc)) continue;
-            int cl[3] = {cc[0], cc[1], cc[2]}, cr[3] = {cc[0], cc[1], cc[2]};
-            cl[a] = p - 1;
-            cr[a] = p;
-            const int tt = S::trans(a, cc[0], cc[1], cc[2]);
-            const int sl = p > 0 ? tile_slot(cl) : S::HOFF(a, 0) + tt;
-            const int sr = p < V[a] ? tile_slot(cr) : S::HOFF(a, 1) + tt;
-            const int Sa = S::S(a);
-            const int base = S::knode(a, 0, k);
-            Real Fh[NC];
-            if (sG[sl] < 0 || sG[sr] < 0) {
-                // outflow boundary: physical flux of the interior trace
-                const bool right_in = sG[sl] < 0;
-                const int si = right_in ? sr : sl;
-                const Real *Lx = right_in ? tLm : tLp;
-                Real u[NC], v[3], rho, pr_, cs;
-#pragma unroll
-                for (int f = 0; f < NC; ++f) {
-                    const Real *q = sU + (f * NSLOT + si) * NP + base;
-                    Real acc = Real(0);
-#pragma unroll
-                    for (int m = 0; m < Q; ++m) acc = fma(Lx[m], q[m * Sa], acc);
-                    u[f] = acc;
-                }
-                if (!primitives<DIM>(u, gamma, rho, v, pr_, cs)) bad = 1;
-                euler_flux<DIM>(u, v, pr_, a, Fh);
-            } else {
-                Real uL[NC + 1], uR[NC + 1];
-                const int nfl = av ? NC + 1 : NC;
-                for (int f = 0; f < nfl; ++f) {
-                    const Real *ql = sU + (f * NSLOT + sl) * NP + base;
-                    const Real *qr = sU + (f * NSLOT + sr) * NP + base;
-                    Real al = Real(0), ar = Real(0);
-#pragma unroll
-                    for (int m = 0; m < Q; ++m) {
-                        al = fma(tLp[m], ql[m * Sa], al);
-                        ar = fma(tLm[m], qr[m * Sa], ar);
-                    }
-                    uL[f] = al;
-                    uR[f] = ar;
-                }
-                if (!hllc<DIM>(uL, uR, gamma, a, Fh)) bad = 1;
-                if (ns || av) {
-                    Real dn[NC];
-                    const Real sc = inv_f / (Real)A.h[a];
-#pragma unroll
-                    for (int f = 0; f < NC; ++f) {
-                        const Real *ql = sU + (f * NSLOT + sl) * NP + base;
-                        const Real *qr = sU + (f * NSLOT + sr) * NP + base;
-                        Real acc = Real(0);
-#pragma unroll
-                        for (int m = 0; m < Q; ++m) acc = fma(tDm[m], ql[m * Sa], fma(tDp[m], qr[m * Sa], acc));
-                        dn[f] = acc * sc;
-                    }
-                    if (ns) {
-                        Real ut[NC], grd[DIM][NC];
-                        const int k0 = k % Q, k1 = k / Q;
-#pragma unroll
-                        for (int f = 0; f < NC; ++f) {
-                            const Real *pf = sUt + (f * NFACE + face) * NPF;
-                            ut[f] = pf[k];
-                            grd[a][f] = dn[f];
-                            // transverse axes in increasing order; face strides 1 and Q
-                            int tb = 0;
-#pragma unroll
-                            for (int bb = 0; bb < DIM; ++bb) {
-                                if (bb == a) continue;
-                                const int kb = tb == 0 ? k0 : k1;
-                                const int sb = tb == 0 ? 1 : Q;
-                                const Real *q = pf + (k - kb * sb);
-                                Real acc = Real(0);
-#pragma unroll
-                                for (int m = 0; m < Q; ++m) acc = fma(tDn[kb * Q + m], q[m * sb], acc);
-                                grd[bb][f] = acc * two_h[bb];
-                                ++tb;
-                            }
-                        }
-                        if (!(ut[0] > Real(0))) bad = 1;
-                        Real Fn[NC];
-                        ns_flux<DIM>(ut, grd, gamma, nu, kappa, a, Fn);
-#pragma unroll
-                        for (int f = 0; f < NC; ++f) Fh[f] -= Fn[f];
-                    }
-                    if (av) {
-                        Real r1, v1[3], p1, c1, r2, v2[3], p2, c2;
-                        primitives<DIM>(uL, gamma, r1, v1, p1, c1);
-                        primitives<DIM>(uR, gamma, r2, v2, p2, c2);
-                        const Real eps = Real(0.5) * epsfac * (clamp01(uL[NC]) * c1 + clamp01(uR[NC]) * c2);
-#pragma unroll
-                        for (int f = 0; f < NC; ++f) Fh[f] -= eps * dn[f];
-                    }
-                }
-            }
-            Real Gp = tG[k % Q];
-            if (DIM == 3) Gp *= tG[k / Q];
-            const Real w = cax[a] * Gp;
-#pragma unroll
-            for (int f = 0; f < NC; ++f) sFh[(f * NFACE + face) * NPF + k] = w * Fh[f];
-        }
-    }
-    __syncthreads();
-
-    // ---- nodal residual: weak divergence of the volume flux + lift of the face fluxes
-    {
-        for (int idx = tid; idx < NC * TC * NP; idx += nth) {
-            const int n = idx % NP;
-            const int fc = idx / NP;
-            const int c = fc % TC, f = fc / TC;
-            if (sG[c] < 0) continue;
-            const int cc[3] = {c % TX, (c / TX) % TY, c / (TX * TY)};
-            Real r = Real(0);
-#pragma unroll
-            for (int a = 0; a < DIM; ++a) {
-                const int Sa = S::S(a);
-                const int i = (n / Sa) % Q;
-                const Real *Fp = sW + ((a * NC + f) * TC + c) * NP + (n - i * Sa);
-#pragma unroll
-                for (int m = 0; m < Q; ++m) r = fma(tWd[i * Q + m], Fp[m * Sa], r);
-                const int tt = S::trans(a, cc[0], cc[1], cc[2]);
-                const int fl = S::FOFF(a) + cc[a] + (S::T(a) + 1) * tt;
-                const int k = S::ktrans(a, n);
-                const Real FL = sFh[(f * NFACE + fl) * NPF + k];
-                const Real FR = sFh[(f * NFACE + fl + 1) * NPF + k];
-                r = fma(tLm[i], FL, r);
-                r = fma(-tLp[i], FR, r);
-            }
-            sR[idx] = r;
-        }
-    }
-    __syncthreads();
-
-    // ---- nodal -> modal (transposed passes) over all fields
-    Real *res;
-    {
-        Real *src = sR, *dst = sW;
-        const int total = nf * TC * NP;
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) {
-            const int Sa = S::S(a);
-            for (int idx = tid; idx < total; idx += nth) {
-                const int l = idx % NP;
-                const int fc = idx / NP;
-                if (sG[fc % TC] < 0) continue;
-                const int la = (l / Sa) % Q;
-                const Real *p = src + fc * NP + (l - la * Sa);
-                Real acc = Real(0);
-#pragma unroll
-                for (int i = 0; i < Q; ++i) acc = fma(tB[i * Q + la], p[i * Sa], acc);
-                dst[idx] = acc;
-            }
-            Real *t = src;
-            src = dst;
-            dst = t;
-            __syncthreads();
-        }
-        res = src;
-    }
-
-    // ---- epilogue: write L or apply the Runge-Kutta stage (delta form)
-    {
-        const int total = nf * TC * NP;
-        const Real dt = A.dtp ? (Real)A.dtp[0] : Real(0);
-        const Real ca = (Real)A.ca, cx = (Real)A.cx, cb = (Real)A.cb;
-        const Real za = (Real)A.za, zx = (Real)A.zx, zb = (Real)A.zb;
-        const Real *di = static_cast<const Real *>(A.din);
-        Real *xb = static_cast<Real *>(A.xbuf);
-        Real *dout = static_cast<Real *>(A.dout);
-        const bool readx = xb && (A.cx != 0.0 || A.zx != 0.0);
-        for (int idx = tid; idx < total; idx += nth) {
-            const int l = idx % NP;
-            const int fc = idx / NP;
-            const int c = fc % TC, f = fc / TC;
-            const int g = sG[c];
-            if (g < 0) continue;
-            const Real L = res[idx];
-            const size_t gi = ((size_t)f * A.ncell + g) * NP + l;
-            if (A.mode == 0) {
-                A.rhs_out[gi] = (double)L;
-                continue;
-            }
-            const Real dtL = dt * L;
-            const Real din = di ? di[gi] : Real(0);
-            const Real x = readx ? xb[gi] : Real(0);
-            const Real dnew = ca * din + cx * x + cb * dtL;
-            if (A.write_z) xb[gi] = za * din + zx * x + zb * dtL;
-            if (A.mode == 1) {
-                dout[gi] = dnew;
-            } else {
-                const double un = A.uold[gi] + (double)dnew;
-                A.unew[gi] = un;
-                if (A.uhi_new) A.uhi_new[gi] = (float)un;
-            }
-        }
-    }
-    if (bad) s_status = 1;
-    __syncthreads();
-    if (tid == 0 && s_status) atomicOr(A.status, DG_STATUS_NONPHYS);
 }
 
 // ------------------------------------------------------------------ step prologue: sensor + CFL speeds
@@ -820,24 +395,6 @@ __global__ void __launch_bounds__(256) prologue_kernel(const PrologueArgs A, con
 }
 
 // ------------------------------------------------------------------ launchers
-
-template <int DIM, int N, typename Real, int TX, int TY, int TZ>
-cudaError_t run_stage(const StageArgs &a, const Tables<Real> &t, cudaStream_t s)
-{
-    using PL = StagePlan<DIM, N, Real, TX, TY, TZ>;
-    auto k = stage_kernel<DIM, N, Real, TX, TY, TZ>;
-    static_assert(PL::BYTES <= 227 * 1024, "stage tile exceeds shared memory");
-    static bool attr_set = false;  // first call comes from the handle set-up, never from a graph capture
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::BYTES);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    const int blocks = a.ntile[0] * a.ntile[1] * a.ntile[2];
-    if (blocks == 0) return cudaSuccess;  // attribute set-up only (done before any graph capture)
-    k<<<blocks, 256, PL::BYTES, s>>>(a, t);
-    return cudaGetLastError();
-}
 
 template <int DIM, int N, typename Real, int TX, int TY, int TZ>
 cudaError_t run_prologue(const PrologueArgs &a, const Tables<Real> &t, cudaStream_t s)

@@ -1,0 +1,629 @@
+// Persistent, line-oriented version of the fused right-hand-side / Runge-Kutta stage kernel.
+//
+// Same arithmetic as stage_kernel (collocated rewriting of the modal sums of
+// Eq. time_stepping_final, see dgx_kernels.cuh); different organisation for sm_103a:
+//  * one CTA loops over tiles; while it works on tile k the state of tile k+1 (u^n and delta,
+//    tile + halo) streams into shared memory with cp.async, so global-load latency is hidden
+//    behind the compute of the current tile;
+//  * the field count and the Navier-Stokes / artificial-viscosity switches are template
+//    parameters, so every field loop unrolls;
+//  * the modal<->nodal transforms work on whole lines of n+1 values: a thread reads its line
+//    once into registers and writes the transformed line back in place (no second buffer, no
+//    (n+1)-fold re-reads of shared memory);
+//  * the last transposed pass (along x, where modes are contiguous) is fused with the
+//    Runge-Kutta epilogue and writes each line of modes with one vector store.
+#pragma once
+
+#include <type_traits>
+
+#include "dgx_kernels.cuh"
+
+namespace dgx {
+
+__device__ __forceinline__ void cp_async_16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_4(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <int DIM, int N, typename Real, bool AV, bool NS, int TX, int TY, int TZ, bool PF>
+struct Stage2Plan {
+    using S = Shape<DIM, N, TX, TY, TZ>;
+    static constexpr int Q = S::Q, NP = S::NP, NPF = S::NPF, NC = S::NC;
+    static constexpr int NF = NC + (AV ? 1 : 0);
+    static constexpr int TC = S::TC, NSLOT = S::NSLOT, NFACE = S::NFACE;
+    static constexpr int TAB = (3 * Q * Q + 7 * Q + 1 + 3) / 4 * 4;
+    static constexpr int SZ_IN = PF ? NF * NSLOT * NP : 0;  // one prefetch array (u^n or delta), tile + halo
+    static constexpr int SZ_U = NF * NSLOT * NP;
+    static constexpr int SZ_F = DIM * NC * TC * NP;
+    static constexpr int SZ_R = NF * TC * NP;
+    static constexpr int SZ_UT = NS ? NC * NFACE * NPF : 0;
+    static constexpr int SZ_FH = NC * NFACE * NPF;
+    static constexpr int OFF_IN0 = TAB;
+    static constexpr int OFF_IN1 = OFF_IN0 + SZ_IN;
+    static constexpr int OFF_U = OFF_IN1 + SZ_IN;
+    static constexpr int OFF_F = OFF_U + SZ_U;
+    static constexpr int OFF_R = OFF_F + SZ_F;
+    static constexpr int OFF_UT = OFF_R + SZ_R;
+    static constexpr int OFF_FH = OFF_UT + SZ_UT;
+    static constexpr int NREAL = (OFF_FH + SZ_FH + 3) / 4 * 4;
+    static constexpr size_t BYTES = sizeof(Real) * (size_t)NREAL + sizeof(int) * 2 * (size_t)NSLOT;
+    // bytes of one cell's modes of one field; async copies use the widest legal chunk
+    static constexpr int CELL_BYTES = NP * (int)sizeof(Real);
+    static constexpr int CHUNK = CELL_BYTES % 16 == 0 ? 16 : (CELL_BYTES % 8 == 0 ? 8 : 4);
+};
+
+template <int DIM, int N, typename Real, bool AV, bool NS, int TX, int TY, int TZ, bool PF>
+__global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Tables<Real> Tg)
+{
+    using S = Shape<DIM, N, TX, TY, TZ>;
+    using PL = Stage2Plan<DIM, N, Real, AV, NS, TX, TY, TZ, PF>;
+    constexpr int Q = S::Q, NP = S::NP, NPF = S::NPF, NC = S::NC, TC = S::TC, NSLOT = S::NSLOT;
+    constexpr int NF = PL::NF, NFACE = S::NFACE;
+    constexpr bool GRAD = AV || NS;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real *sm = reinterpret_cast<Real *>(smem_raw);
+    Real *tB = sm, *tDn = tB + Q * Q, *tWd = tDn + Q * Q, *tG = tWd + Q * Q;
+    Real *tLp = tG + Q, *tLm = tLp + Q, *tCm = tLm + Q, *tCp = tCm + Q, *tDm = tCp + Q, *tDp = tDm + Q;
+    Real *sIn0 = sm + PL::OFF_IN0, *sIn1 = sm + PL::OFF_IN1, *sU = sm + PL::OFF_U, *sF = sm + PL::OFF_F;
+    Real *sR = sm + PL::OFF_R, *sUt = sm + PL::OFF_UT, *sFh = sm + PL::OFF_FH;
+    int *sGa = reinterpret_cast<int *>(sm + PL::NREAL);
+    int *sGb = sGa + NSLOT;
+    __shared__ int s_status;
+
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int ntiles = A.ntile[0] * A.ntile[1] * A.ntile[2];
+    const Real *ub = static_cast<const Real *>(A.ubase);
+    const Real *di = static_cast<const Real *>(A.din);
+
+    for (int i = tid; i < Q * Q; i += nth) {
+        tB[i] = Tg.B[i / Q][i % Q];
+        tDn[i] = Tg.Dn[i / Q][i % Q];
+        tWd[i] = Tg.Wd[i / Q][i % Q];
+    }
+    for (int i = tid; i < Q; i += nth) {
+        tG[i] = Tg.G[i];
+        tLp[i] = Tg.Lp[i];
+        tLm[i] = Tg.Lm[i];
+        tCm[i] = Tg.Cm[i];
+        tCp[i] = Tg.Cp[i];
+        tDm[i] = Tg.Dm[i];
+        tDp[i] = Tg.Dp[i];
+    }
+    if (tid == 0) s_status = 0;
+
+    auto tile_origin = [&](int tile, int *o, int *V) {
+        int b = tile;
+        const int tx = b % A.ntile[0];
+        b /= A.ntile[0];
+        const int ty = b % A.ntile[1];
+        const int tz = b / A.ntile[1];
+        o[0] = tx * TX;
+        o[1] = ty * TY;
+        o[2] = tz * TZ;
+        V[0] = min(TX, A.N[0] - o[0]);
+        V[1] = min(TY, A.N[1] - o[1]);
+        V[2] = DIM == 3 ? min(TZ, A.N[2] - o[2]) : 1;
+    };
+
+    // slot indices of a tile, then asynchronous copies of its stage state into sIn0 / sIn1
+    // (called by all threads of the CTA)
+    auto issue_tile = [&](int tile, int *sG) {
+        int o[3], V[3];
+        tile_origin(tile, o, V);
+        for (int s = tid; s < NSLOT; s += nth) sG[s] = slot_global<S>(s, o, V, A.N, A.bc);
+        __syncthreads();
+        if constexpr (!PF) return;  // without prefetch buffers the tile is loaded at the top of its iteration
+        constexpr int PER = PL::CELL_BYTES / PL::CHUNK;  // chunks per (field, cell)
+        constexpr int TOTAL = NF * NSLOT * PER;
+        for (int idx = tid; idx < TOTAL; idx += nth) {
+            const int c = idx % PER;
+            const int fs = idx / PER;
+            const int slot = fs % NSLOT, f = fs / NSLOT;
+            const int g = sG[slot];
+            if (g < 0) continue;
+            const size_t gbyte = (((size_t)f * A.ncell + g) * NP) * sizeof(Real) + (size_t)c * PL::CHUNK;
+            const size_t sbyte = ((size_t)(f * NSLOT + slot) * NP) * sizeof(Real) + (size_t)c * PL::CHUNK;
+            const char *gu = reinterpret_cast<const char *>(ub) + gbyte;
+            char *su = reinterpret_cast<char *>(sIn0) + sbyte;
+            if (PL::CHUNK == 16) cp_async_16(su, gu);
+            else if (PL::CHUNK == 8) cp_async_8(su, gu);
+            else cp_async_4(su, gu);
+            if (di) {
+                const char *gd = reinterpret_cast<const char *>(di) + gbyte;
+                char *sd = reinterpret_cast<char *>(sIn1) + sbyte;
+                if (PL::CHUNK == 16) cp_async_16(sd, gd);
+                else if (PL::CHUNK == 8) cp_async_8(sd, gd);
+                else cp_async_4(sd, gd);
+            }
+        }
+        cp_async_commit();
+    };
+
+    const Real gamma = (Real)A.gamma, nu = (Real)A.nu, kappa = (Real)A.kappa;
+    const Real epsfac = (Real)(A.av_scale * A.hmin / (N + 1));
+    const Real inv_tau = (Real)((N + 1) / (A.f_tau * A.hmin));
+    const Real f_v = (Real)A.f_v;
+    const Real inv_f = Tg.inv_f;
+    Real two_h[3], cax[3], inv_h[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        two_h[a] = (Real)(2.0 / A.h[a]);
+        inv_h[a] = (Real)(1.0 / A.h[a]);
+        cax[a] = (Real)((DIM == 2 ? 0.5 : 0.25) / A.h[a]);
+    }
+    const Real src_w = (Real)(DIM == 2 ? 0.25 : 0.125);
+    const Real dt = (A.mode != 0 && A.dtp) ? (Real)A.dtp[0] : Real(0);
+    const Real ca = (Real)A.ca, cx = (Real)A.cx, cb = (Real)A.cb;
+    const Real za = (Real)A.za, zx = (Real)A.zx, zb = (Real)A.zb;
+    Real *xb = static_cast<Real *>(A.xbuf);
+    Real *dout = static_cast<Real *>(A.dout);
+    const bool readx = xb && (A.cx != 0.0 || A.zx != 0.0);
+    int bad = 0;
+
+    int tile = blockIdx.x;
+    int *sG = sGa, *sGn = sGb;
+    __syncthreads();
+    if (tile < ntiles) issue_tile(tile, sG);
+
+    while (tile < ntiles) {
+        int o[3], V[3];
+        tile_origin(tile, o, V);
+        if constexpr (PF) {
+            cp_async_wait_all();
+            __syncthreads();
+        } else {
+            // synchronous load of u^n (+ delta) of tile and halo into sU
+            for (int idx = tid; idx < NF * NSLOT * NP; idx += nth) {
+                const int l = idx % NP;
+                const int fs = idx / NP;
+                const int g = sG[fs % NSLOT];
+                if (g < 0) continue;
+                const size_t gi = ((size_t)(fs / NSLOT) * A.ncell + g) * NP + l;
+                sU[idx] = ub[gi] + (di ? di[gi] : Real(0));
+            }
+            __syncthreads();
+        }
+
+        // ---- pass A: x-lines, modal -> nodal, from the loaded input (u^n + delta)
+        {
+            constexpr int LINES = NF * NSLOT * (NP / Q);
+            for (int idx = tid; idx < LINES; idx += nth) {
+                const int fs = idx / (NP / Q);
+                const int r = idx % (NP / Q);
+                if (sG[fs % NSLOT] < 0) continue;
+                const int base = fs * NP + r * Q;
+                Real w[Q];
+#pragma unroll
+                for (int m = 0; m < Q; ++m) {
+                    if constexpr (PF) w[m] = sIn0[base + m] + (di ? sIn1[base + m] : Real(0));
+                    else w[m] = sU[base + m];
+                }
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    Real acc = Real(0);
+#pragma unroll
+                    for (int m = 0; m < Q; ++m) acc = fma(tB[i * Q + m], w[m], acc);
+                    sU[base + i] = acc;
+                }
+            }
+        }
+        __syncthreads();
+        // the input buffers are free: start streaming the next tile
+        const int next = tile + gridDim.x;
+        if (PF && next < ntiles) issue_tile(next, sGn);
+
+        // ---- passes B (y) and C (z) in place
+#pragma unroll
+        for (int a = 1; a < DIM; ++a) {
+            const int Sa = S::S(a);
+            constexpr int LINES = NF * NSLOT * (NP / Q);
+            for (int idx = tid; idx < LINES; idx += nth) {
+                const int fs = idx / (NP / Q);
+                const int r = idx % (NP / Q);
+                if (sG[fs % NSLOT] < 0) continue;
+                // r enumerates the (Q^(d-1)) positions transverse to axis a
+                const int lo = r % Sa, hi = r / Sa;
+                const int base = fs * NP + lo + hi * Sa * Q;
+                Real w[Q];
+#pragma unroll
+                for (int m = 0; m < Q; ++m) w[m] = sU[base + m * Sa];
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    Real acc = Real(0);
+#pragma unroll
+                    for (int m = 0; m < Q; ++m) acc = fma(tB[i * Q + m], w[m], acc);
+                    sU[base + i * Sa] = acc;
+                }
+            }
+            __syncthreads();
+        }
+
+        // ---- pointwise volume fluxes and alpha source; recovered interface state (NS)
+        {
+            constexpr int NODES = TC * NP;
+            for (int idx = tid; idx < NODES; idx += nth) {
+                const int c = idx / NP, j = idx % NP;
+                const int g = sG[c];
+                if (g < 0) continue;
+                Real u[NC + 1];
+#pragma unroll
+                for (int f = 0; f < NF; ++f) u[f] = sU[(f * NSLOT + c) * NP + j];
+                Real gr[DIM][NC];
+                if (GRAD) {
+#pragma unroll
+                    for (int a = 0; a < DIM; ++a) {
+                        const int Sa = S::S(a);
+                        const int i = (j / Sa) % Q;
+                        const int base = j - i * Sa;
+#pragma unroll
+                        for (int f = 0; f < NC; ++f) {
+                            const Real *p = sU + (f * NSLOT + c) * NP + base;
+                            Real acc = Real(0);
+#pragma unroll
+                            for (int m = 0; m < Q; ++m) acc = fma(tDn[i * Q + m], p[m * Sa], acc);
+                            gr[a][f] = acc * two_h[a];
+                        }
+                    }
+                }
+                Real rho, v[3], p, cs;
+                if (!primitives<DIM>(u, gamma, rho, v, p, cs)) bad = 1;
+                const Real eps = AV ? epsfac * clamp01(u[NC]) * cs : Real(0);
+                const int jj[3] = {j % Q, (j / Q) % Q, j / (Q * Q)};
+                Real Gv = Real(1);
+#pragma unroll
+                for (int a = 0; a < DIM; ++a) Gv *= tG[jj[a]];
+#pragma unroll
+                for (int a = 0; a < DIM; ++a) {
+                    Real F[NC];
+                    euler_flux<DIM>(u, v, p, a, F);
+                    if (NS) {
+                        Real Fn[NC];
+                        ns_flux<DIM>(u, gr, gamma, nu, kappa, a, Fn);
+#pragma unroll
+                        for (int f = 0; f < NC; ++f) F[f] -= Fn[f];
+                    }
+                    if (AV) {
+#pragma unroll
+                        for (int f = 0; f < NC; ++f) F[f] -= eps * gr[a][f];
+                    }
+                    Real Gp = Real(1);
+#pragma unroll
+                    for (int q = 0; q < DIM; ++q)
+                        if (q != a) Gp *= tG[jj[q]];
+                    const Real w = cax[a] * Gp;
+#pragma unroll
+                    for (int f = 0; f < NC; ++f) sF[((a * NC + f) * TC + c) * NP + j] = w * F[f];
+                }
+                if (AV) {
+                    Real div = Real(0);
+#pragma unroll
+                    for (int a = 0; a < DIM; ++a) div += (gr[a][1 + a] - v[a] * gr[a][0]) / rho;
+                    const Real adot = f_v * fmax(Real(0), -div) + (Real)A.wig[g] - u[NC] * cs * inv_tau;
+                    sR[(NC * TC + c) * NP + j] = src_w * Gv * adot;
+                }
+            }
+            if (NS) {
+                // recovered state at every face point, one loop per axis with the axis known at compile time
+                auto recover_axis = [&](auto axc) {
+                    constexpr int a = decltype(axc)::value;
+                    constexpr int Sa = S::S(a);
+                    constexpr int FA = S::NFA(a);
+                    for (int q = tid; q < NC * FA * NPF; q += nth) {
+                        const int k = q % NPF;
+                        const int fc = q / NPF;
+                        const int fl = fc % FA, f = fc / FA;
+                        const int pp = fl % (S::T(a) + 1);
+                        const int t = fl / (S::T(a) + 1);
+                        int cc[3] = {0, 0, 0};
+                        S::untrans(a, t, cc);
+                        bool ok = pp <= V[a];
+#pragma unroll
+                        for (int b2 = 0; b2 < 3; ++b2)
+                            if (b2 != a && cc[b2] >= V[b2]) ok = false;
+                        if (!ok) continue;
+                        int cl[3] = {cc[0], cc[1], cc[2]}, cr[3] = {cc[0], cc[1], cc[2]};
+                        cl[a] = pp - 1;
+                        cr[a] = pp;
+                        const int sl = pp > 0 ? cl[0] + TX * (cl[1] + TY * cl[2]) : S::HOFF(a, 0) + t;
+                        const int sr = pp < V[a] ? cr[0] + TX * (cr[1] + TY * cr[2]) : S::HOFF(a, 1) + t;
+                        if (sG[sl] < 0 || sG[sr] < 0) continue;
+                        const int base = S::knode(a, 0, k);
+                        const Real *pl = sU + (f * NSLOT + sl) * NP + base;
+                        const Real *pr = sU + (f * NSLOT + sr) * NP + base;
+                        Real acc = Real(0);
+#pragma unroll
+                        for (int m = 0; m < Q; ++m) acc = fma(tCm[m], pl[m * Sa], fma(tCp[m], pr[m * Sa], acc));
+                        sUt[(f * NFACE + S::FOFF(a) + fl) * NPF + k] = acc;
+                    }
+                };
+                recover_axis(std::integral_constant<int, 0>{});
+                recover_axis(std::integral_constant<int, 1>{});
+                if constexpr (DIM == 3) recover_axis(std::integral_constant<int, 2>{});
+            }
+        }
+        __syncthreads();
+
+        // ---- face fluxes (HLLC - recovered dissipative flux), pre-weighted for the lift
+        auto flux_axis = [&](auto axc) {
+          constexpr int a = decltype(axc)::value;
+          constexpr int FA = S::NFA(a);
+          for (int idx = tid; idx < FA * NPF; idx += nth) {
+            const int k = idx % NPF, fl = idx / NPF;
+            const int face = S::FOFF(a) + fl;
+            const int pp = fl % (S::T(a) + 1);
+            const int t = fl / (S::T(a) + 1);
+            int cc[3] = {0, 0, 0};
+            S::untrans(a, t, cc);
+            bool ok = pp <= V[a];
+#pragma unroll
+            for (int b2 = 0; b2 < 3; ++b2)
+                if (b2 != a && cc[b2] >= V[b2]) ok = false;
+            if (!ok) continue;
+            int cl[3] = {cc[0], cc[1], cc[2]}, cr[3] = {cc[0], cc[1], cc[2]};
+            cl[a] = pp - 1;
+            cr[a] = pp;
+            const int sl = pp > 0 ? cl[0] + TX * (cl[1] + TY * cl[2]) : S::HOFF(a, 0) + t;
+            const int sr = pp < V[a] ? cr[0] + TX * (cr[1] + TY * cr[2]) : S::HOFF(a, 1) + t;
+            const int Sa = S::S(a);
+            const int base = S::knode(a, 0, k);
+            Real Fh[NC];
+            if (sG[sl] < 0 || sG[sr] < 0) {
+                const bool right_in = sG[sl] < 0;
+                const int si = right_in ? sr : sl;
+                const Real *Lx = right_in ? tLm : tLp;
+                Real u[NC], v[3], rho, pr_, cs;
+#pragma unroll
+                for (int f = 0; f < NC; ++f) {
+                    const Real *q = sU + (f * NSLOT + si) * NP + base;
+                    Real acc = Real(0);
+#pragma unroll
+                    for (int m = 0; m < Q; ++m) acc = fma(Lx[m], q[m * Sa], acc);
+                    u[f] = acc;
+                }
+                if (!primitives<DIM>(u, gamma, rho, v, pr_, cs)) bad = 1;
+                euler_flux<DIM>(u, v, pr_, a, Fh);
+            } else {
+                Real uL[NC + 1], uR[NC + 1];
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    const Real *ql = sU + (f * NSLOT + sl) * NP + base;
+                    const Real *qr = sU + (f * NSLOT + sr) * NP + base;
+                    Real al = Real(0), ar = Real(0);
+#pragma unroll
+                    for (int m = 0; m < Q; ++m) {
+                        al = fma(tLp[m], ql[m * Sa], al);
+                        ar = fma(tLm[m], qr[m * Sa], ar);
+                    }
+                    uL[f] = al;
+                    uR[f] = ar;
+                }
+                if (!hllc<DIM>(uL, uR, gamma, a, Fh)) bad = 1;
+                if (GRAD) {
+                    Real dn[NC];
+                    const Real sc = inv_f * inv_h[a];
+#pragma unroll
+                    for (int f = 0; f < NC; ++f) {
+                        const Real *ql = sU + (f * NSLOT + sl) * NP + base;
+                        const Real *qr = sU + (f * NSLOT + sr) * NP + base;
+                        Real acc = Real(0);
+#pragma unroll
+                        for (int m = 0; m < Q; ++m) acc = fma(tDm[m], ql[m * Sa], fma(tDp[m], qr[m * Sa], acc));
+                        dn[f] = acc * sc;
+                    }
+                    if (NS) {
+                        Real ut[NC], grd[DIM][NC];
+                        const int k0 = k % Q, k1 = k / Q;
+#pragma unroll
+                        for (int f = 0; f < NC; ++f) {
+                            const Real *pf = sUt + (f * NFACE + face) * NPF;
+                            ut[f] = pf[k];
+#pragma unroll
+                            for (int bb = 0; bb < DIM; ++bb) grd[bb][f] = Real(0);
+                            grd[a][f] = dn[f];
+                            int tb = 0;
+#pragma unroll
+                            for (int bb = 0; bb < DIM; ++bb) {
+                                if (bb == a) continue;
+                                const int kb = tb == 0 ? k0 : k1;
+                                const int sb = tb == 0 ? 1 : Q;
+                                const Real *q = pf + (k - kb * sb);
+                                Real acc = Real(0);
+#pragma unroll
+                                for (int m = 0; m < Q; ++m) acc = fma(tDn[kb * Q + m], q[m * sb], acc);
+                                grd[bb][f] = acc * two_h[bb];
+                                ++tb;
+                            }
+                        }
+                        if (!(ut[0] > Real(0))) bad = 1;
+                        Real Fn[NC];
+                        ns_flux<DIM>(ut, grd, gamma, nu, kappa, a, Fn);
+#pragma unroll
+                        for (int f = 0; f < NC; ++f) Fh[f] -= Fn[f];
+                    }
+                    if (AV) {
+                        Real r1, v1[3], p1, c1, r2, v2[3], p2, c2;
+                        primitives<DIM>(uL, gamma, r1, v1, p1, c1);
+                        primitives<DIM>(uR, gamma, r2, v2, p2, c2);
+                        const Real eps = Real(0.5) * epsfac * (clamp01(uL[NC]) * c1 + clamp01(uR[NC]) * c2);
+#pragma unroll
+                        for (int f = 0; f < NC; ++f) Fh[f] -= eps * dn[f];
+                    }
+                }
+            }
+            Real Gp = tG[k % Q];
+            if (DIM == 3) Gp *= tG[k / Q];
+            const Real w = cax[a] * Gp;
+#pragma unroll
+            for (int f = 0; f < NC; ++f) sFh[(f * NFACE + face) * NPF + k] = w * Fh[f];
+          }
+        };
+        flux_axis(std::integral_constant<int, 0>{});
+        flux_axis(std::integral_constant<int, 1>{});
+        if constexpr (DIM == 3) flux_axis(std::integral_constant<int, 2>{});
+        __syncthreads();
+
+        // ---- nodal residual of the conserved fields: weak divergence + lift
+        for (int idx = tid; idx < NC * TC * NP; idx += nth) {
+            const int n = idx % NP;
+            const int fc = idx / NP;
+            const int c = fc % TC, f = fc / TC;
+            if (sG[c] < 0) continue;
+            const int cc[3] = {c % TX, (c / TX) % TY, c / (TX * TY)};
+            Real r = Real(0);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                const int Sa = S::S(a);
+                const int i = (n / Sa) % Q;
+                const Real *Fp = sF + ((a * NC + f) * TC + c) * NP + (n - i * Sa);
+#pragma unroll
+                for (int m = 0; m < Q; ++m) r = fma(tWd[i * Q + m], Fp[m * Sa], r);
+                const int tt = S::trans(a, cc[0], cc[1], cc[2]);
+                const int fl = S::FOFF(a) + cc[a] + (S::T(a) + 1) * tt;
+                const int k = S::ktrans(a, n);
+                r = fma(tLm[i], sFh[(f * NFACE + fl) * NPF + k], r);
+                r = fma(-tLp[i], sFh[(f * NFACE + fl + 1) * NPF + k], r);
+            }
+            sR[idx] = r;
+        }
+        __syncthreads();
+
+        // ---- nodal -> modal: transposed passes along z and y in place
+#pragma unroll
+        for (int a = DIM - 1; a >= 1; --a) {
+            const int Sa = S::S(a);
+            constexpr int LINES = NF * TC * (NP / Q);
+            for (int idx = tid; idx < LINES; idx += nth) {
+                const int fc = idx / (NP / Q);
+                const int r = idx % (NP / Q);
+                if (sG[fc % TC] < 0) continue;
+                const int lo = r % Sa, hi = r / Sa;
+                const int base = fc * NP + lo + hi * Sa * Q;
+                Real w[Q];
+#pragma unroll
+                for (int m = 0; m < Q; ++m) w[m] = sR[base + m * Sa];
+#pragma unroll
+                for (int l = 0; l < Q; ++l) {
+                    Real acc = Real(0);
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) acc = fma(tB[i * Q + l], w[i], acc);
+                    sR[base + l * Sa] = acc;
+                }
+            }
+            __syncthreads();
+        }
+
+        // ---- last transposed pass along x fused with the Runge-Kutta epilogue
+        {
+            constexpr int LINES = NF * TC * (NP / Q);
+            for (int idx = tid; idx < LINES; idx += nth) {
+                const int fc = idx / (NP / Q);
+                const int r = idx % (NP / Q);
+                const int c = fc % TC, f = fc / TC;
+                const int g = sG[c];
+                if (g < 0) continue;
+                const int base = fc * NP + r * Q;
+                Real w[Q], L[Q];
+#pragma unroll
+                for (int m = 0; m < Q; ++m) w[m] = sR[base + m];
+#pragma unroll
+                for (int l = 0; l < Q; ++l) {
+                    Real acc = Real(0);
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) acc = fma(tB[i * Q + l], w[i], acc);
+                    L[l] = acc;
+                }
+                const size_t gi = ((size_t)f * A.ncell + g) * NP + (size_t)r * Q;
+                if (A.mode == 0) {
+#pragma unroll
+                    for (int l = 0; l < Q; ++l) A.rhs_out[gi + l] = (double)L[l];
+                    continue;
+                }
+#pragma unroll
+                for (int l = 0; l < Q; ++l) {
+                    const Real dtL = dt * L[l];
+                    const Real din = di ? di[gi + l] : Real(0);
+                    const Real x = readx ? xb[gi + l] : Real(0);
+                    const Real dnew = ca * din + cx * x + cb * dtL;
+                    if (A.write_z) xb[gi + l] = za * din + zx * x + zb * dtL;
+                    if (A.mode == 1) {
+                        dout[gi + l] = dnew;
+                    } else {
+                        const double un = A.uold[gi + l] + (double)dnew;
+                        A.unew[gi + l] = un;
+                        if (A.uhi_new) A.uhi_new[gi + l] = (float)un;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if constexpr (PF) {
+            int *t = sG;
+            sG = sGn;
+            sGn = t;
+        } else if (next < ntiles) {
+            issue_tile(next, sG);  // slot map of the next tile (loaded at the top of the loop)
+        }
+        tile = next;
+    }
+    cp_async_wait_all();
+    if (bad) s_status = 1;
+    __syncthreads();
+    if (tid == 0 && s_status) atomicOr(A.status, DG_STATUS_NONPHYS);
+}
+
+template <int DIM, int N, typename Real, bool AV, bool NS, int TX, int TY, int TZ>
+cudaError_t run_stage2(const StageArgs &a, const Tables<Real> &t, cudaStream_t s)
+{
+    // prefetch buffers when the tile still fits in shared memory with them
+    constexpr bool PF = Stage2Plan<DIM, N, Real, AV, NS, TX, TY, TZ, true>::BYTES <= 227 * 1024;
+    using PL = Stage2Plan<DIM, N, Real, AV, NS, TX, TY, TZ, PF>;
+    auto k = stage2_kernel<DIM, N, Real, AV, NS, TX, TY, TZ, PF>;
+    static_assert(PL::BYTES <= 227 * 1024, "stage2 tile exceeds shared memory");
+    static int blocks_per_sm = 0;
+    static int sms = 0;
+    if (!blocks_per_sm) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::BYTES);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k, 256, PL::BYTES);
+        if (e != cudaSuccess) return e;
+        if (blocks_per_sm < 1) blocks_per_sm = 1;
+    }
+    const int tiles = a.ntile[0] * a.ntile[1] * a.ntile[2];
+    if (tiles == 0) return cudaSuccess;
+    const int grid = tiles < sms * blocks_per_sm ? tiles : sms * blocks_per_sm;
+    k<<<grid, 256, PL::BYTES, s>>>(a, t);
+    return cudaGetLastError();
+}
+
+// run-time (AV, NS) dispatch onto the compile-time variants
+template <int DIM, int N, typename Real, int TX, int TY, int TZ>
+cudaError_t run_stage2_any(const StageArgs &a, const Tables<Real> &t, cudaStream_t s)
+{
+    if (a.av_on) {
+        if (a.ns_on) return run_stage2<DIM, N, Real, true, true, TX, TY, TZ>(a, t, s);
+        return run_stage2<DIM, N, Real, true, false, TX, TY, TZ>(a, t, s);
+    }
+    if (a.ns_on) return run_stage2<DIM, N, Real, false, true, TX, TY, TZ>(a, t, s);
+    return run_stage2<DIM, N, Real, false, false, TX, TY, TZ>(a, t, s);
+}
+
+}  // namespace dgx
