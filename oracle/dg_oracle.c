@@ -44,9 +44,10 @@
  *    points of the state at the start of the step, h = min_alpha h_alpha;
  *  - SSP Runge-Kutta: P stages for P <= 3 (forward Euler, Heun, Shu-Osher
  *    RK3) and the 5-stage 4th-order scheme of Spiteri & Ruuth (2002) above;
- *  - positivity limiter (Sec. 4.2): applied after every stage to the
- *    conserved fields' higher modes; rho_b = 1e-6 mean rho, p_b = 1e-6 p(mean
- *    state); pressure pass halves the higher modes, at most 60 times;
+ *  - positivity limiter (Sec. 4.2): applied to the state entering each step
+ *    and after every stage, to the conserved fields' higher modes; rho_b =
+ *    1e-6 mean rho, p_b = 1e-6 p(mean state); pressure pass halves the higher
+ *    modes, at most 60 times;
  *  - outflow boundary: the ghost trace equals the interior trace, so the face
  *    flux is the physical flux of the interior trace and no dissipative flux
  *    crosses the boundary.
@@ -978,6 +979,10 @@ int or_step(const or_cfg *c, double *w, double *S_prev, double *wig, double *sca
     if (or_rk_table(s, al, be)) return OR_EINVAL;
     size_t nw = (size_t)g.FT * g.ncell * g.M;
     int status = OR_OK;
+    /* the limiter also acts on the state entering the step: after the first
+     * step that state is a limited stage output, so this only changes
+     * initial data (a projected discontinuity can be negative at points) */
+    if (c->positivity_on) status |= or_positivity(c, w);
     if (c->av_on) status |= or_wiggle(c, w, S_prev, wig, scal[0], (long)scal[1]);
     if (!(dt > 0.0)) status |= or_max_dt(c, w, &dt);
     if (status & OR_EINVAL) return status;
