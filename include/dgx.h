@@ -76,7 +76,9 @@ typedef struct dg_grid {
  *             1, 2, 3, 5 explicitly.
  *  av_on:     1 adds the alpha field and artificial viscosity (Sec. 4.1).
  *  positivity_on: 1 applies the positivity limiter of Sec. 4.2 after every
- *             stage (this build: DG_EUNSUPPORTED from dg_set_params). */
+ *             stage (rho_bottom = 1e-6 mean rho, p_bottom = 1e-6 p(mean state),
+ *             at most 60 pressure halvings; a cell that still fails, or whose
+ *             mean state is non-physical, sets the status word). */
 typedef struct dg_params {
     int precision;
     int rk_stages;

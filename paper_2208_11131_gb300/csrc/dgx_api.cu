@@ -352,6 +352,15 @@ cudaError_t launch_prologue_any(const dg_t *h, int update_sensor)
                    : launch_prologue_3d_f64(h->degree, a, h->td, h->stream);
 }
 
+cudaError_t launch_limiter_any(const dg_t *h, const LimiterArgs &a)
+{
+    if (h->dim == 2)
+        return fp32(h) ? launch_limiter_2d_f32(h->degree, a, h->tf, h->stream)
+                       : launch_limiter_2d_f64(h->degree, a, h->td, h->stream);
+    return fp32(h) ? launch_limiter_3d_f32(h->degree, a, h->tf, h->stream)
+                   : launch_limiter_3d_f64(h->degree, a, h->td, h->stream);
+}
+
 // set the dynamic shared-memory attribute of this handle's kernels (launch with zero tiles)
 int prepare_kernels(dg_t *h)
 {
@@ -367,6 +376,9 @@ int prepare_kernels(dg_t *h)
     else
         CK(h, fp32(h) ? launch_prologue_3d_f32(h->degree, pa, h->tf, h->stream)
                       : launch_prologue_3d_f64(h->degree, pa, h->td, h->stream));
+    LimiterArgs la;
+    memset(&la, 0, sizeof la);
+    CK(h, launch_limiter_any(h, la));
     return DG_OK;
 }
 
@@ -379,6 +391,18 @@ int enqueue_step(dg_t *h, double dt, cudaEvent_t *ev = nullptr)
     const Schedule S = schedule_for(stage_count(h));
     if (!S.stages) return fail(h, DG_EINVAL, "unsupported Runge-Kutta stage count %d", stage_count(h));
     if (ev) CK(h, cudaEventRecord(ev[0], h->stream));
+    if (h->p.positivity_on) {
+        // the state entering the step is limited too (only initial data can need it)
+        LimiterArgs la;
+        memset(&la, 0, sizeof la);
+        la.ncell = h->ncell;
+        la.gamma = h->gamma;
+        la.last = 1;
+        la.ufull = h->U[h->cur];
+        la.uhi = fp32(h) ? h->Uhi[h->cur] : nullptr;
+        la.status = h->status;
+        CK(h, launch_limiter_any(h, la));
+    }
     CK(h, launch_prologue_any(h, 1));
     if (ev) CK(h, cudaEventRecord(ev[1], h->stream));
     dt_kernel<<<1, 256, 0, h->stream>>>(h->partial, h->pblocks, dt > 0.0 ? dt : 0.0, h->p.cfl, h->hmin,
@@ -406,6 +430,19 @@ int enqueue_step(dg_t *h, double dt, cudaEvent_t *ev = nullptr)
         a.unew = h->U[nx];
         a.uhi_new = fp32(h) ? h->Uhi[nx] : nullptr;
         CK(h, launch_stage_any(h, a));
+        if (h->p.positivity_on) {
+            LimiterArgs la;
+            memset(&la, 0, sizeof la);
+            la.ncell = h->ncell;
+            la.gamma = h->gamma;
+            la.last = d.last;
+            la.ubase = a.ubase;
+            la.delta = d.last ? nullptr : h->D[d.out];
+            la.ufull = d.last ? h->U[nx] : nullptr;
+            la.uhi = d.last && fp32(h) ? h->Uhi[nx] : nullptr;
+            la.status = h->status;
+            CK(h, launch_limiter_any(h, la));
+        }
         if (ev) CK(h, cudaEventRecord(ev[3 + i], h->stream));
     }
     h->cur = nx;
@@ -541,7 +578,7 @@ int dg_set_params(dg_t *h, const dg_params *p)
         (p->rk_stages != 0 && p->rk_stages != 1 && p->rk_stages != 2 && p->rk_stages != 3 && p->rk_stages != 5) ||
         (p->av_on != 0 && p->av_on != 1) || !(p->f_tau > 0.0) || p->av_scale < 0.0)
         return fail(h, DG_EINVAL, "invalid dg_params");
-    if (p->positivity_on) return fail(h, DG_EUNSUPPORTED, "the positivity limiter is not built yet");
+    if (p->positivity_on != 0 && p->positivity_on != 1) return fail(h, DG_EINVAL, "positivity_on must be 0 or 1");
     const bool realloc = p->precision != h->p.precision || p->av_on != h->p.av_on;
     h->p = *p;
     if (h->graph) {

@@ -2,6 +2,7 @@
 // (dimension, precision) pair.  The including unit defines
 //   DGX_DIM, DGX_REAL, DGX_SUFFIX and DGX_TILES(X) with one
 //   X(degree, stage TX,TY,TZ, prologue TX,TY,TZ) entry per degree 0..5.
+#include "dgx_limiter.cuh"
 #include "dgx_stage2.cuh"
 
 // DGX_STAGE_RUN selects the stage kernel of the unit: run_stage2_any (persistent, prefetching,
@@ -19,6 +20,9 @@ namespace dgx {
 #define DGX_PRO_CASE(n, sx, sy, sz, px, py, pz) \
     case n:                                     \
         return run_prologue<DGX_DIM, n, DGX_REAL, px, py, pz>(a, t, s);
+#define DGX_LIM_CASE(n, sx, sy, sz, px, py, pz) \
+    case n:                                    \
+        return run_limiter<DGX_DIM, n, DGX_REAL>(a, t, s);
 #define DGX_TILE_CASE(n, sx, sy, sz, px, py, pz) \
     case n:                                      \
         st[0] = sx;                              \
@@ -40,6 +44,13 @@ cudaError_t DGX_CAT(launch_prologue_, DGX_SUFFIX)(int degree, const PrologueArgs
                                                   cudaStream_t s)
 {
     switch (degree) { DGX_TILES(DGX_PRO_CASE) }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t DGX_CAT(launch_limiter_, DGX_SUFFIX)(int degree, const LimiterArgs &a, const Tables<DGX_REAL> &t,
+                                                 cudaStream_t s)
+{
+    switch (degree) { DGX_TILES(DGX_LIM_CASE) }
     return cudaErrorInvalidValue;
 }
 

@@ -87,6 +87,18 @@ struct PrologueArgs {
     int *status;
 };
 
+// Arguments of the positivity-limiter kernel (Sec. 4.2), run after a stage.
+struct LimiterArgs {
+    long long ncell;
+    double gamma;
+    int last;            // 1: limit u^{n+1} (FP64 u, plus the FP32 copy in bulk mode); 0: u_base + delta
+    const void *ubase;   // Real*: stage base (u_hi in bulk mode, u^n in FP64)
+    void *delta;         // Real*: stage delta, limited in place
+    double *ufull;       // FP64 state, limited in place (last stage)
+    float *uhi;          // FP32 copy of ufull to refresh (bulk mode, last stage) or null
+    int *status;
+};
+
 struct LaunchCfg {
     int blocks;
     int threads;
@@ -109,6 +121,10 @@ cudaError_t launch_prologue_2d_f64(int degree, const PrologueArgs &a, const Tabl
 cudaError_t launch_prologue_2d_f32(int degree, const PrologueArgs &a, const Tables<float> &t, cudaStream_t s);
 cudaError_t launch_prologue_3d_f64(int degree, const PrologueArgs &a, const Tables<double> &t, cudaStream_t s);
 cudaError_t launch_prologue_3d_f32(int degree, const PrologueArgs &a, const Tables<float> &t, cudaStream_t s);
+cudaError_t launch_limiter_2d_f64(int degree, const LimiterArgs &a, const Tables<double> &t, cudaStream_t s);
+cudaError_t launch_limiter_2d_f32(int degree, const LimiterArgs &a, const Tables<float> &t, cudaStream_t s);
+cudaError_t launch_limiter_3d_f64(int degree, const LimiterArgs &a, const Tables<double> &t, cudaStream_t s);
+cudaError_t launch_limiter_3d_f32(int degree, const LimiterArgs &a, const Tables<float> &t, cudaStream_t s);
 void tiles_2d_f64(int degree, int *stage, int *pro);
 void tiles_2d_f32(int degree, int *stage, int *pro);
 void tiles_3d_f64(int degree, int *stage, int *pro);

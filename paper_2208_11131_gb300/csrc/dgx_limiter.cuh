@@ -1,0 +1,196 @@
+// Positivity limiter of Sec. 4.2, applied to a Runge-Kutta stage state, one warp per cell.
+//
+// For every cell: rho_bottom = 1e-6 mean(rho) and p_bottom = 1e-6 p(mean state).  The state is
+// evaluated at the volume Gauss points and at the Gauss points of the 2d faces -- all of them
+// points of the tensor grid {x_1..x_Q, -1, +1}^d with at most one coordinate at +-1 -- by d
+// sum-factorised passes that widen one axis at a time from Q to Q+2 values.  If the minimum
+// density is below rho_bottom, the higher modes of every conserved field are scaled by
+// theta = (mean - rho_bottom) / (mean - rho_min).  Then the higher modes are halved until the
+// minimum pressure is at least p_bottom, at most 60 times.  Along u(s) = mean + s (u - mean)
+// the pressure is concave in s and above p_bottom at s = 0, so each point needs all halvings
+// up to its own first admissible one; the cell takes the largest count.  The total factor
+// theta 2^-k is applied in one multiplication (halving is exact, so this is the same as
+// scaling by theta and halving k times).
+#pragma once
+
+#include "dgx_kernels.cuh"
+
+namespace dgx {
+
+
+template <int DIM, int N, typename Real>
+struct LimiterPlan {
+    static constexpr int Q = N + 1;
+    static constexpr int E = Q + 2;  // Gauss points, then -1, then +1
+    static constexpr int NP = DIM == 2 ? Q * Q : Q * Q * Q;
+    static constexpr int NE = DIM == 2 ? E * E : E * E * E;
+    static constexpr int NC = DIM + 2;
+    static constexpr size_t PER_CELL = sizeof(Real) * (size_t)NC * (NP + 2 * NE);
+    static constexpr int CPB_RAW = (int)((96 * 1024) / PER_CELL);
+    static constexpr int CPB = CPB_RAW >= 8 ? 8 : (CPB_RAW < 1 ? 1 : CPB_RAW);  // cells (= warps) per CTA
+    static constexpr size_t BYTES = sizeof(Real) * (size_t)(E * Q) + PER_CELL * CPB;
+};
+
+template <int DIM, int N, typename Real>
+__global__ void limiter_kernel(const LimiterArgs A, const Tables<Real> Tg)
+{
+    using PL = LimiterPlan<DIM, N, Real>;
+    constexpr int Q = PL::Q, E = PL::E, NP = PL::NP, NE = PL::NE, NC = PL::NC;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real *tE = reinterpret_cast<Real *>(smem_raw);  // [E][Q]: Pt_m at x_i, then at -1, +1
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Real *sM = tE + E * Q + (size_t)warp * NC * (NP + 2 * NE);
+    Real *sA = sM + NC * NP;
+    Real *sB = sA + NC * NE;
+
+    for (int i = threadIdx.x; i < E * Q; i += blockDim.x) {
+        const int r = i / Q, m = i % Q;
+        if (r < Q) {
+            tE[i] = Tg.B[r][m];
+        } else {
+            // Pt_m(-1) = (-1)^m sqrt(2m+1), Pt_m(+1) = sqrt(2m+1)
+            const Real s = sqrt(Real(2 * m + 1));
+            tE[i] = (r == Q && (m & 1)) ? -s : s;
+        }
+    }
+    __syncthreads();
+
+    const long long cell = (long long)blockIdx.x * PL::CPB + warp;
+    if (cell >= A.ncell) return;
+    const Real *ub = static_cast<const Real *>(A.ubase);
+    Real *dl = static_cast<Real *>(A.delta);
+    for (int i = lane; i < NC * NP; i += 32) {
+        const int f = i / NP, l = i % NP;
+        const size_t gi = ((size_t)f * A.ncell + cell) * NP + l;
+        sM[i] = A.last ? (Real)A.ufull[gi] : ub[gi] + dl[gi];
+    }
+    __syncwarp();
+
+    // widen axis 0, then 1 (then 2): Q -> E values per line
+    {
+        // pass x: sM [Q^d] -> sA [E * Q^(d-1)]
+        constexpr int LX = NP / Q;
+        for (int i = lane; i < NC * LX * E; i += 32) {
+            const int r = i % E, fl = i / E;
+            const Real *p = sM + fl * Q;
+            Real acc = Real(0);
+#pragma unroll
+            for (int m = 0; m < Q; ++m) acc = fma(tE[r * Q + m], p[m], acc);
+            sA[fl * E + r] = acc;
+        }
+        __syncwarp();
+        // pass y: sA [E, Q, (Q)] -> sB [E, E, (Q)]
+        constexpr int TZ = DIM == 3 ? Q : 1;
+        for (int i = lane; i < NC * E * E * TZ; i += 32) {
+            const int ix = i % E;
+            const int ry = (i / E) % E;
+            const int rest = i / (E * E);  // f * TZ + z
+            const Real *p = sA + rest * (E * Q) + ix;
+            Real acc = Real(0);
+#pragma unroll
+            for (int m = 0; m < Q; ++m) acc = fma(tE[ry * Q + m], p[m * E], acc);
+            sB[rest * (E * E) + ry * E + ix] = acc;
+        }
+        __syncwarp();
+        if (DIM == 3) {
+            // pass z: sB [E, E, Q] -> sA [E, E, E]
+            for (int i = lane; i < NC * NE; i += 32) {
+                const int ixy = i % (E * E);
+                const int rz = (i / (E * E)) % E;
+                const int f = i / NE;
+                const Real *p = sB + f * (E * E * Q) + ixy;
+                Real acc = Real(0);
+#pragma unroll
+                for (int m = 0; m < Q; ++m) acc = fma(tE[rz * Q + m], p[m * E * E], acc);
+                sA[f * NE + rz * E * E + ixy] = acc;
+            }
+            __syncwarp();
+        }
+    }
+    const Real *pts = DIM == 3 ? sA : sB;  // [NC][NE] values on the widened grid
+
+    const Real gamma = (Real)A.gamma;
+    Real mean[NC];
+#pragma unroll
+    for (int f = 0; f < NC; ++f) mean[f] = sM[f * NP];
+    Real rb, vb[3], pbar, cb;
+    const bool ok_mean = primitives<DIM>(mean, gamma, rb, vb, pbar, cb);
+    const Real rho_b = Real(1e-6) * mean[0], p_b = Real(1e-6) * pbar;
+
+    // a point of the widened grid is used when at most one coordinate is at +-1
+    auto used = [&](int i) {
+        const int c0 = i % E, c1 = (i / E) % E, c2 = DIM == 3 ? i / (E * E) : 0;
+        return (c0 >= Q) + (c1 >= Q) + (c2 >= Q) <= 1;
+    };
+    Real rmin = Real(1e30);
+    for (int i = lane; i < NE; i += 32)
+        if (used(i)) rmin = fmin(rmin, pts[i]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) rmin = fmin(rmin, __shfl_xor_sync(0xffffffffu, rmin, off));
+    const Real theta = rmin < rho_b ? (mean[0] - rho_b) / (mean[0] - rmin) : Real(1);
+
+    int kmax = 0;
+    bool fail = false;
+    for (int i = lane; i < NE; i += 32) {
+        if (!used(i)) continue;
+        Real dv[NC];
+#pragma unroll
+        for (int f = 0; f < NC; ++f) dv[f] = pts[f * NE + i] - mean[f];
+        int k = 0;
+        for (; k <= 60; ++k) {
+            const Real s = ldexp(theta, -k);
+            Real u[NC];
+#pragma unroll
+            for (int f = 0; f < NC; ++f) u[f] = mean[f] + s * dv[f];
+            Real ke = Real(0);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) ke += u[1 + a] * u[1 + a];
+            const Real p = (gamma - Real(1)) * (u[DIM + 1] - Real(0.5) * ke / u[0]);
+            if (p >= p_b) break;
+        }
+        if (k > 60) {
+            fail = true;
+            k = 60;
+        }
+        kmax = max(kmax, k);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, off));
+    fail = __any_sync(0xffffffffu, fail);
+    if (lane == 0 && (!ok_mean || fail)) atomicOr(A.status, DG_STATUS_NONPHYS);
+    if (!ok_mean || (theta == Real(1) && kmax == 0)) return;
+
+    const Real sc = ldexp(theta, -kmax);
+    for (int i = lane; i < NC * NP; i += 32) {
+        const int f = i / NP, l = i % NP;
+        if (l == 0) continue;
+        const size_t gi = ((size_t)f * A.ncell + cell) * NP + l;
+        if (A.last) {
+            const double u = A.ufull[gi] * (double)sc;
+            A.ufull[gi] = u;
+            if (A.uhi) A.uhi[gi] = (float)u;
+        } else {
+            // limited stage state sc * (u_base + delta), expressed as a new delta over u_base
+            dl[gi] = sc * sM[i] - ub[gi];
+        }
+    }
+}
+
+template <int DIM, int N, typename Real>
+cudaError_t run_limiter(const LimiterArgs &a, const Tables<Real> &t, cudaStream_t s)
+{
+    using PL = LimiterPlan<DIM, N, Real>;
+    auto k = limiter_kernel<DIM, N, Real>;
+    static bool attr_set = false;  // first call comes from the handle set-up
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (a.ncell == 0) return cudaSuccess;
+    const long long blocks = (a.ncell + PL::CPB - 1) / PL::CPB;
+    k<<<(unsigned)blocks, 32 * PL::CPB, PL::BYTES, s>>>(a, t);
+    return cudaGetLastError();
+}
+
+}  // namespace dgx
