@@ -136,7 +136,9 @@ int dg_steps(dg_t *h, int nsteps, double dt);
 /* One step as dg_step, timed: CUDA events are recorded on the handle's stream
  * around each launch of the step and the call waits for the last one.
  * ms[0] = step prologue (oscillation sensor + CFL speeds), ms[1] = time-step
- * reduction, ms[2 + i] = fused right-hand-side / Runge-Kutta stage i.
+ * reduction, ms[2 + i] = fused right-hand-side / Runge-Kutta stage i.  With
+ * two or more stages and the limiter off, the prologue work is done inside
+ * stage 0 (ms[0] = 0, ms[2] includes it) and the reduction runs after it.
  * nms must be at least 2 + the stage count (at most 7).  For profiling and
  * benchmarks; the arithmetic is identical to dg_step. */
 int dg_step_timed(dg_t *h, double dt, float *ms, int nms);

@@ -38,7 +38,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     os.makedirs(BUILD, exist_ok=True)
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) +
-                     glob.glob(os.path.join(ROOT, "include", "*.h")))
+                     glob.glob(os.path.join(ROOT, "include", "*.h")) + [os.path.abspath(__file__)])
     nvcc = _nvcc()
     procs = []
     objs = []
@@ -46,7 +46,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
-            cmd = [nvcc] + ARCH + FLAGS + (["-Xptxas", "-v"] if ptxas_info else []) + ["-c", src, "-o", obj]
+            # the FP32-bulk kernels use the fast single-precision division and square root
+            # (2 ulp, denormals flushed); FP64 arithmetic is unaffected by these flags
+            extra = ["--use_fast_math"] if src.endswith("_f32.cu") else []
+            cmd = [nvcc] + ARCH + FLAGS + extra + (["-Xptxas", "-v"] if ptxas_info else []) + ["-c", src, "-o", obj]
             log = open(obj + ".log", "w")
             procs.append((subprocess.Popen(cmd, stdout=log, stderr=subprocess.STDOUT), obj, log))
     failed = []

@@ -142,6 +142,7 @@ __global__ void sums_final_kernel(const double *partial, int nblk, int nc, doubl
 }
 
 constexpr int kSumBlocks = 256;
+constexpr int kMaxStageGrid = 16384;  // persistent stage grid: SMs x resident CTAs (upper bound)
 
 }  // namespace
 
@@ -168,6 +169,9 @@ struct dg_handle {
     double *Sprev = nullptr, *wig = nullptr;
     double *dtp = nullptr;  // {dt, step, t, dt query}
     double *partial = nullptr;
+    int partial_cap = 0;
+    int fused_last = 0;  // the last enqueued step folded the prologue into its first stage
+    int nev = 0;         // events recorded by the last timed step
     double *sums = nullptr;  // [kSumBlocks*nc] partials + [nc] result
     double *rhs_tmp = nullptr;
     int *status = nullptr;
@@ -270,7 +274,8 @@ int alloc_buffers(dg_t *h)
         h->pgrid[a] = (Na + pt[a] - 1) / pt[a];
     }
     h->pblocks = h->pgrid[0] * h->pgrid[1] * h->pgrid[2];
-    if (!st) st = al((void **)&h->partial, 2 * (size_t)h->pblocks * sizeof(double));
+    h->partial_cap = h->pblocks > kMaxStageGrid ? h->pblocks : kMaxStageGrid;
+    if (!st) st = al((void **)&h->partial, 2 * (size_t)h->partial_cap * sizeof(double));
     if (!st) st = al((void **)&h->sums, ((size_t)kSumBlocks * h->nc + h->nc) * sizeof(double));
     if (!st) st = al((void **)&h->status, sizeof(int));
     if (st) {
@@ -316,13 +321,13 @@ void base_stage_args(const dg_t *h, StageArgs &a)
     a.status = h->status;
 }
 
-cudaError_t launch_stage_any(const dg_t *h, const StageArgs &a)
+cudaError_t launch_stage_any(const dg_t *h, const StageArgs &a, int *grid = nullptr)
 {
     if (h->dim == 2)
-        return fp32(h) ? launch_stage_2d_f32(h->degree, a, h->tf, h->stream)
-                       : launch_stage_2d_f64(h->degree, a, h->td, h->stream);
-    return fp32(h) ? launch_stage_3d_f32(h->degree, a, h->tf, h->stream)
-                   : launch_stage_3d_f64(h->degree, a, h->td, h->stream);
+        return fp32(h) ? launch_stage_2d_f32(h->degree, a, h->tf, h->stream, grid)
+                       : launch_stage_2d_f64(h->degree, a, h->td, h->stream, grid);
+    return fp32(h) ? launch_stage_3d_f32(h->degree, a, h->tf, h->stream, grid)
+                   : launch_stage_3d_f64(h->degree, a, h->td, h->stream, grid);
 }
 
 cudaError_t launch_prologue_any(const dg_t *h, int update_sensor)
@@ -384,31 +389,40 @@ int prepare_kernels(dg_t *h)
 
 int stage_count(const dg_t *h) { return h->p.rk_stages > 0 ? h->p.rk_stages : auto_stages(h->degree); }
 
-// enqueue one full step on h->stream (no host synchronisation); with `ev`, record an event
-// before the first launch and after every launch (prologue, dt, each stage)
+// enqueue one full step on h->stream (no host synchronisation).  With `ev`, an event is recorded
+// before the first launch (ev[0]) and after each launch in launch order (ev[1..]).
+//
+// With two or more stages and no limiter, the step prologue (sensor, wiggle source, CFL speeds of
+// u^n) is folded into the first stage kernel, which then stores L(u^n) unscaled because dt is not
+// known yet; the dt reduction runs right after it and the second stage scales the stored first
+// delta by its Runge-Kutta coefficient times dt.
 int enqueue_step(dg_t *h, double dt, cudaEvent_t *ev = nullptr)
 {
     const Schedule S = schedule_for(stage_count(h));
     if (!S.stages) return fail(h, DG_EINVAL, "unsupported Runge-Kutta stage count %d", stage_count(h));
-    if (ev) CK(h, cudaEventRecord(ev[0], h->stream));
-    if (h->p.positivity_on) {
-        // the state entering the step is limited too (only initial data can need it)
-        LimiterArgs la;
-        memset(&la, 0, sizeof la);
-        la.ncell = h->ncell;
-        la.gamma = h->gamma;
-        la.last = 1;
-        la.ufull = h->U[h->cur];
-        la.uhi = fp32(h) ? h->Uhi[h->cur] : nullptr;
-        la.status = h->status;
-        CK(h, launch_limiter_any(h, la));
+    const bool fused = S.stages >= 2 && !h->p.positivity_on;
+    int ne = 0;
+    if (ev) CK(h, cudaEventRecord(ev[ne++], h->stream));
+    if (!fused) {
+        if (h->p.positivity_on) {
+            // the state entering the step is limited too (only initial data can need it)
+            LimiterArgs la;
+            memset(&la, 0, sizeof la);
+            la.ncell = h->ncell;
+            la.gamma = h->gamma;
+            la.last = 1;
+            la.ufull = h->U[h->cur];
+            la.uhi = fp32(h) ? h->Uhi[h->cur] : nullptr;
+            la.status = h->status;
+            CK(h, launch_limiter_any(h, la));
+        }
+        CK(h, launch_prologue_any(h, 1));
+        if (ev) CK(h, cudaEventRecord(ev[ne++], h->stream));
+        dt_kernel<<<1, 256, 0, h->stream>>>(h->partial, h->pblocks, dt > 0.0 ? dt : 0.0, h->p.cfl, h->hmin,
+                                            h->degree + 1, h->dtp, 1, h->status);
+        CK(h, cudaGetLastError());
+        if (ev) CK(h, cudaEventRecord(ev[ne++], h->stream));
     }
-    CK(h, launch_prologue_any(h, 1));
-    if (ev) CK(h, cudaEventRecord(ev[1], h->stream));
-    dt_kernel<<<1, 256, 0, h->stream>>>(h->partial, h->pblocks, dt > 0.0 ? dt : 0.0, h->p.cfl, h->hmin,
-                                        h->degree + 1, h->dtp, 1, h->status);
-    CK(h, cudaGetLastError());
-    if (ev) CK(h, cudaEventRecord(ev[2], h->stream));
     const int c = h->cur, nx = 1 - h->cur;
     for (int i = 0; i < S.stages; ++i) {
         const StageDesc &d = S.s[i];
@@ -429,7 +443,22 @@ int enqueue_step(dg_t *h, double dt, cudaEvent_t *ev = nullptr)
         a.uold = h->U[c];
         a.unew = h->U[nx];
         a.uhi_new = fp32(h) ? h->Uhi[nx] : nullptr;
-        CK(h, launch_stage_any(h, a));
+        if (fused && i == 0) {
+            a.fused = 1;
+            a.partial = h->partial;
+            a.S_prev = h->Sprev;
+            a.wig_w = h->wig;
+            a.f_w = h->p.f_w;
+            a.s_on = h->p.s_onset / ((double)(h->degree + 1) * (h->degree + 1));
+            a.epi_unit_dt = 1;  // delta_1 := L(u^n); scaled by cb dt where it is read
+            a.cb = 1.0;
+        }
+        if (fused && i == 1) {
+            a.din_dt = 1;
+            a.din_coef = S.s[0].cb;
+        }
+        int grid = 0;
+        CK(h, launch_stage_any(h, a, &grid));
         if (h->p.positivity_on) {
             LimiterArgs la;
             memset(&la, 0, sizeof la);
@@ -443,8 +472,17 @@ int enqueue_step(dg_t *h, double dt, cudaEvent_t *ev = nullptr)
             la.status = h->status;
             CK(h, launch_limiter_any(h, la));
         }
-        if (ev) CK(h, cudaEventRecord(ev[3 + i], h->stream));
+        if (ev) CK(h, cudaEventRecord(ev[ne++], h->stream));
+        if (fused && i == 0) {
+            if (grid > h->partial_cap) return fail(h, DG_EINVAL, "stage grid %d exceeds %d", grid, h->partial_cap);
+            dt_kernel<<<1, 256, 0, h->stream>>>(h->partial, grid, dt > 0.0 ? dt : 0.0, h->p.cfl, h->hmin,
+                                                h->degree + 1, h->dtp, 1, h->status);
+            CK(h, cudaGetLastError());
+            if (ev) CK(h, cudaEventRecord(ev[ne++], h->stream));
+        }
     }
+    h->fused_last = fused ? 1 : 0;
+    h->nev = ne;
     h->cur = nx;
     return DG_OK;
 }
@@ -729,14 +767,25 @@ int dg_steps(dg_t *h, int nsteps, double dt)
 int dg_step_timed(dg_t *h, double dt, float *ms, int nms)
 {
     if (!h || !ms) return DG_EINVAL;
-    const int nl = 2 + stage_count(h);
+    const int ns = stage_count(h);
+    const int nl = 2 + ns;
     if (nms < nl) return fail(h, DG_EINVAL, "dg_step_timed needs room for %d launch times", nl);
     for (int i = 0; i <= nl; ++i)
         if (!h->ev[i]) CK(h, cudaEventCreate(&h->ev[i]));
     int st = enqueue_step(h, dt, h->ev);
     if (st) return st;
-    CK(h, cudaEventSynchronize(h->ev[nl]));
-    for (int i = 0; i < nl; ++i) CK(h, cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]));
+    CK(h, cudaEventSynchronize(h->ev[h->nev - 1]));
+    float d[8];
+    for (int i = 0; i + 1 < h->nev; ++i) CK(h, cudaEventElapsedTime(&d[i], h->ev[i], h->ev[i + 1]));
+    if (h->fused_last) {
+        // launch order: stage 1 (with the prologue work), dt reduction, stages 2..s
+        ms[0] = 0.0f;
+        ms[2] = d[0];
+        ms[1] = d[1];
+        for (int i = 1; i < ns; ++i) ms[2 + i] = d[1 + i];
+    } else {
+        for (int i = 0; i < nl; ++i) ms[i] = d[i];
+    }
     return DG_OK;
 }
 

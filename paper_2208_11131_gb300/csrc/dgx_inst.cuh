@@ -16,7 +16,7 @@ namespace dgx {
 
 #define DGX_STAGE_CASE(n, sx, sy, sz, px, py, pz) \
     case n:                                       \
-        return DGX_STAGE_RUN<DGX_DIM, n, DGX_REAL, sx, sy, sz>(a, t, s);
+        return DGX_STAGE_RUN<DGX_DIM, n, DGX_REAL, sx, sy, sz>(a, t, s, grid);
 #define DGX_PRO_CASE(n, sx, sy, sz, px, py, pz) \
     case n:                                     \
         return run_prologue<DGX_DIM, n, DGX_REAL, px, py, pz>(a, t, s);
@@ -34,7 +34,7 @@ namespace dgx {
         return;
 
 cudaError_t DGX_CAT(launch_stage_, DGX_SUFFIX)(int degree, const StageArgs &a, const Tables<DGX_REAL> &t,
-                                               cudaStream_t s)
+                                               cudaStream_t s, int *grid)
 {
     switch (degree) { DGX_TILES(DGX_STAGE_CASE) }
     return cudaErrorInvalidValue;

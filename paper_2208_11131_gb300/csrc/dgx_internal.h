@@ -68,6 +68,19 @@ struct StageArgs {
     float *uhi_new;      // FP32 copy of u^{n+1} (bulk mode) or null
 
     int *status;
+
+    // first stage of a step with the prologue folded in: sensor + wiggle source per cell and
+    // per-CTA maxima of c_s and |v| of u^n; the stage stores L(u^n) itself (dt not yet known)
+    int fused;
+    double *partial;   // [gridDim.x][2]
+    double *S_prev;    // sensor history (read, then updated)
+    double *wig_w;     // wiggle source (written)
+    double f_w, s_on;
+    int epi_unit_dt;   // epilogue uses dt = 1 (delta_out = L when cb = 1)
+    // the stored input delta is din_coef * dt times the true one's 1/(din_coef dt)-scaled value:
+    // true delta = din_coef * dtp[0] * din when din_dt is set
+    int din_dt;
+    double din_coef;
 };
 
 // Arguments of the step-prologue kernel (CFL speeds + oscillation sensor).
@@ -113,10 +126,10 @@ cudaError_t launch_prologue(int dim, int degree, int prec, const PrologueArgs &a
 void stage_tiles(int dim, int degree, int prec, int tile[3]);
 void prologue_tiles(int dim, int degree, int prec, int tile[3]);
 
-cudaError_t launch_stage_2d_f64(int degree, const StageArgs &a, const Tables<double> &t, cudaStream_t s);
-cudaError_t launch_stage_2d_f32(int degree, const StageArgs &a, const Tables<float> &t, cudaStream_t s);
-cudaError_t launch_stage_3d_f64(int degree, const StageArgs &a, const Tables<double> &t, cudaStream_t s);
-cudaError_t launch_stage_3d_f32(int degree, const StageArgs &a, const Tables<float> &t, cudaStream_t s);
+cudaError_t launch_stage_2d_f64(int degree, const StageArgs &a, const Tables<double> &t, cudaStream_t s, int *grid);
+cudaError_t launch_stage_2d_f32(int degree, const StageArgs &a, const Tables<float> &t, cudaStream_t s, int *grid);
+cudaError_t launch_stage_3d_f64(int degree, const StageArgs &a, const Tables<double> &t, cudaStream_t s, int *grid);
+cudaError_t launch_stage_3d_f32(int degree, const StageArgs &a, const Tables<float> &t, cudaStream_t s, int *grid);
 cudaError_t launch_prologue_2d_f64(int degree, const PrologueArgs &a, const Tables<double> &t, cudaStream_t s);
 cudaError_t launch_prologue_2d_f32(int degree, const PrologueArgs &a, const Tables<float> &t, cudaStream_t s);
 cudaError_t launch_prologue_3d_f64(int degree, const PrologueArgs &a, const Tables<double> &t, cudaStream_t s);

@@ -130,9 +130,9 @@ __device__ __forceinline__ void euler_flux(const Real *u, const Real *v, Real p,
 // Written without pointers to local arrays and without early returns: the side values that enter
 // the star state are chosen by value selects, so every array stays in registers.
 template <int DIM, typename Real>
-__device__ __forceinline__ bool hllc(const Real *uL, const Real *uR, Real gamma, int a, Real *F)
+__device__ __forceinline__ bool hllc(const Real *uL, const Real *uR, Real gamma, int a, Real *F, Real &cL, Real &cR)
 {
-    Real rL, rR, pL, pR, cL, cR, vL[3], vR[3];
+    Real rL, rR, pL, pR, vL[3], vR[3];
     bool ok = primitives<DIM>(uL, gamma, rL, vL, pL, cL);
     ok = primitives<DIM>(uR, gamma, rR, vR, pR, cR) && ok;
     Real vnL = vL[0], vnR = vR[0];
@@ -175,6 +175,13 @@ __device__ __forceinline__ bool hllc(const Real *uL, const Real *uR, Real gamma,
         for (int f = 0; f < DIM + 2; ++f) F[f] += SK * (us[f] - uK[f]);
     }
     return ok;
+}
+
+template <int DIM, typename Real>
+__device__ __forceinline__ bool hllc(const Real *uL, const Real *uR, Real gamma, int a, Real *F)
+{
+    Real cL, cR;
+    return hllc<DIM>(uL, uR, gamma, a, F, cL, cR);
 }
 
 // Navier-Stokes flux along axis a (Sec. 3.3): (0, Pi_a, v.Pi_a + kappa (gamma-1) rho d_a u_int),

@@ -58,7 +58,8 @@ struct Stage2Plan {
     static constexpr int OFF_R = OFF_F + SZ_F;
     static constexpr int OFF_UT = OFF_R + SZ_R;
     static constexpr int OFF_FH = OFF_UT + SZ_UT;
-    static constexpr int NREAL = (OFF_FH + SZ_FH + 3) / 4 * 4;
+    static constexpr int OFF_WIG = OFF_FH + SZ_FH;
+    static constexpr int NREAL = (OFF_WIG + TC + 3) / 4 * 4;
     static constexpr size_t BYTES = sizeof(Real) * (size_t)NREAL + sizeof(int) * 2 * (size_t)NSLOT;
     // bytes of one cell's modes of one field; async copies use the widest legal chunk
     static constexpr int CELL_BYTES = NP * (int)sizeof(Real);
@@ -79,7 +80,8 @@ __global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Ta
     Real *tB = sm, *tDn = tB + Q * Q, *tWd = tDn + Q * Q, *tG = tWd + Q * Q;
     Real *tLp = tG + Q, *tLm = tLp + Q, *tCm = tLm + Q, *tCp = tCm + Q, *tDm = tCp + Q, *tDp = tDm + Q;
     Real *sIn0 = sm + PL::OFF_IN0, *sIn1 = sm + PL::OFF_IN1, *sU = sm + PL::OFF_U, *sF = sm + PL::OFF_F;
-    Real *sR = sm + PL::OFF_R, *sUt = sm + PL::OFF_UT, *sFh = sm + PL::OFF_FH;
+    Real *sR = sm + PL::OFF_R, *sUt = sm + PL::OFF_UT, *sFh = sm + PL::OFF_FH, *sWig = sm + PL::OFF_WIG;
+    __shared__ double s_red[2][8];
     int *sGa = reinterpret_cast<int *>(sm + PL::NREAL);
     int *sGb = sGa + NSLOT;
     __shared__ int s_status;
@@ -166,7 +168,9 @@ __global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Ta
         cax[a] = (Real)((DIM == 2 ? 0.5 : 0.25) / A.h[a]);
     }
     const Real src_w = (Real)(DIM == 2 ? 0.25 : 0.125);
-    const Real dt = (A.mode != 0 && A.dtp) ? (Real)A.dtp[0] : Real(0);
+    const Real dt = A.epi_unit_dt ? Real(1) : ((A.mode != 0 && A.dtp) ? (Real)A.dtp[0] : Real(0));
+    const Real dsc = A.din_dt ? (Real)(A.din_coef * A.dtp[0]) : Real(1);  // stored delta -> true delta
+    Real cmax = Real(0), vmax = Real(0);  // CFL speeds (fused first stage)
     const Real ca = (Real)A.ca, cx = (Real)A.cx, cb = (Real)A.cb;
     const Real za = (Real)A.za, zx = (Real)A.zx, zb = (Real)A.zb;
     Real *xb = static_cast<Real *>(A.xbuf);
@@ -193,9 +197,47 @@ __global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Ta
                 const int g = sG[fs % NSLOT];
                 if (g < 0) continue;
                 const size_t gi = ((size_t)(fs / NSLOT) * A.ncell + g) * NP + l;
-                sU[idx] = ub[gi] + (di ? di[gi] : Real(0));
+                sU[idx] = ub[gi] + (di ? dsc * di[gi] : Real(0));
             }
             __syncthreads();
+        }
+        // wiggle source per tile cell: from the sensor of u^n (fused first stage) or as stored
+        auto cell_wiggle = [&](const Real *modal) {
+            for (int c = tid; c < TC; c += nth) {
+                const int g = sG[c];
+                if (g < 0) continue;
+                if (!A.fused) {
+                    sWig[c] = (Real)A.wig[g];
+                    continue;
+                }
+                Real hi = Real(0), all = Real(0);
+                const Real *w0 = modal + c * NP;  // density field, slot c
+#pragma unroll
+                for (int l = 0; l < NP; ++l) {
+                    const int l0 = l % Q, l1 = (l / Q) % Q, l2 = DIM == 3 ? l / (Q * Q) : 0;
+                    const bool top = N > 0 && (l0 == N || l1 == N || (DIM == 3 && l2 == N));
+                    all += w0[l] * w0[l];
+                    if (top) hi += w0[l] * w0[l];
+                }
+                const double Sk = all > Real(0) ? (double)(hi / all) : 0.0;
+                const double dt_prev = A.dtp[0], step = A.dtp[1];
+                const double s_floor = 1e-4 * A.s_on;
+                double dlog = 0.0;
+                if (step > 0.0 && dt_prev > 0.0)
+                    dlog = (log(fmax(Sk, s_floor)) - log(fmax(A.S_prev[g], s_floor))) / dt_prev;
+                const double wg = (Sk > A.s_on) ? A.f_w * fmax(0.0, dlog) : 0.0;
+                A.wig_w[g] = wg;
+                A.S_prev[g] = Sk;
+                sWig[c] = (Real)wg;
+            }
+        };
+        if constexpr (!PF) {
+            if (AV) {
+                cell_wiggle(sU);
+                __syncthreads();
+            }
+        } else if (AV) {
+            cell_wiggle(sIn0);  // the modal u^n stays in sIn0 during pass A (first stage: no delta)
         }
 
         // ---- pass A: x-lines, modal -> nodal, from the loaded input (u^n + delta)
@@ -209,7 +251,7 @@ __global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Ta
                 Real w[Q];
 #pragma unroll
                 for (int m = 0; m < Q; ++m) {
-                    if constexpr (PF) w[m] = sIn0[base + m] + (di ? sIn1[base + m] : Real(0));
+                    if constexpr (PF) w[m] = sIn0[base + m] + (di ? dsc * sIn1[base + m] : Real(0));
                     else w[m] = sU[base + m];
                 }
 #pragma unroll
@@ -281,6 +323,13 @@ __global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Ta
                 }
                 Real rho, v[3], p, cs;
                 if (!primitives<DIM>(u, gamma, rho, v, p, cs)) bad = 1;
+                if (A.fused) {
+                    Real v2 = Real(0);
+#pragma unroll
+                    for (int a = 0; a < DIM; ++a) v2 += v[a] * v[a];
+                    cmax = fmax(cmax, cs);
+                    vmax = fmax(vmax, sqrt(v2));
+                }
                 const Real eps = AV ? epsfac * clamp01(u[NC]) * cs : Real(0);
                 const int jj[3] = {j % Q, (j / Q) % Q, j / (Q * Q)};
                 Real Gv = Real(1);
@@ -312,7 +361,7 @@ __global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Ta
                     Real div = Real(0);
 #pragma unroll
                     for (int a = 0; a < DIM; ++a) div += (gr[a][1 + a] - v[a] * gr[a][0]) / rho;
-                    const Real adot = f_v * fmax(Real(0), -div) + (Real)A.wig[g] - u[NC] * cs * inv_tau;
+                    const Real adot = f_v * fmax(Real(0), -div) + sWig[c] - u[NC] * cs * inv_tau;
                     sR[(NC * TC + c) * NP + j] = src_w * Gv * adot;
                 }
             }
@@ -411,7 +460,8 @@ __global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Ta
                     uL[f] = al;
                     uR[f] = ar;
                 }
-                if (!hllc<DIM>(uL, uR, gamma, a, Fh)) bad = 1;
+                Real cL, cR;  // trace sound speeds, reused by the artificial viscosity below
+                if (!hllc<DIM>(uL, uR, gamma, a, Fh, cL, cR)) bad = 1;
                 if (GRAD) {
                     Real dn[NC];
                     const Real sc = inv_f * inv_h[a];
@@ -455,10 +505,7 @@ __global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Ta
                         for (int f = 0; f < NC; ++f) Fh[f] -= Fn[f];
                     }
                     if (AV) {
-                        Real r1, v1[3], p1, c1, r2, v2[3], p2, c2;
-                        primitives<DIM>(uL, gamma, r1, v1, p1, c1);
-                        primitives<DIM>(uR, gamma, r2, v2, p2, c2);
-                        const Real eps = Real(0.5) * epsfac * (clamp01(uL[NC]) * c1 + clamp01(uR[NC]) * c2);
+                        const Real eps = Real(0.5) * epsfac * (clamp01(uL[NC]) * cL + clamp01(uR[NC]) * cR);
 #pragma unroll
                         for (int f = 0; f < NC; ++f) Fh[f] -= eps * dn[f];
                     }
@@ -555,7 +602,7 @@ __global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Ta
 #pragma unroll
                 for (int l = 0; l < Q; ++l) {
                     const Real dtL = dt * L[l];
-                    const Real din = di ? di[gi + l] : Real(0);
+                    const Real din = di ? dsc * di[gi + l] : Real(0);
                     const Real x = readx ? xb[gi + l] : Real(0);
                     const Real dnew = ca * din + cx * x + cb * dtL;
                     if (A.write_z) xb[gi + l] = za * din + zx * x + zb * dtL;
@@ -581,12 +628,33 @@ __global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Ta
     }
     cp_async_wait_all();
     if (bad) s_status = 1;
+    if (A.fused) {
+        double c = (double)cmax, v = (double)vmax;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            c = fmax(c, __shfl_xor_sync(0xffffffffu, c, off));
+            v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+        }
+        if ((tid & 31) == 0) {
+            s_red[0][tid >> 5] = c;
+            s_red[1][tid >> 5] = v;
+        }
+    }
     __syncthreads();
     if (tid == 0 && s_status) atomicOr(A.status, DG_STATUS_NONPHYS);
+    if (A.fused && tid == 0) {
+        double c = 0.0, v = 0.0;
+        for (int w = 0; w < nth / 32; ++w) {
+            c = fmax(c, s_red[0][w]);
+            v = fmax(v, s_red[1][w]);
+        }
+        A.partial[2 * blockIdx.x + 0] = c;
+        A.partial[2 * blockIdx.x + 1] = v;
+    }
 }
 
 template <int DIM, int N, typename Real, bool AV, bool NS, int TX, int TY, int TZ>
-cudaError_t run_stage2(const StageArgs &a, const Tables<Real> &t, cudaStream_t s)
+cudaError_t run_stage2(const StageArgs &a, const Tables<Real> &t, cudaStream_t s, int *grid_out)
 {
     // prefetch buffers when the tile still fits in shared memory with them
     constexpr bool PF = Stage2Plan<DIM, N, Real, AV, NS, TX, TY, TZ, true>::BYTES <= 227 * 1024;
@@ -610,20 +678,21 @@ cudaError_t run_stage2(const StageArgs &a, const Tables<Real> &t, cudaStream_t s
     const int tiles = a.ntile[0] * a.ntile[1] * a.ntile[2];
     if (tiles == 0) return cudaSuccess;
     const int grid = tiles < sms * blocks_per_sm ? tiles : sms * blocks_per_sm;
+    if (grid_out) *grid_out = grid;
     k<<<grid, 256, PL::BYTES, s>>>(a, t);
     return cudaGetLastError();
 }
 
 // run-time (AV, NS) dispatch onto the compile-time variants
 template <int DIM, int N, typename Real, int TX, int TY, int TZ>
-cudaError_t run_stage2_any(const StageArgs &a, const Tables<Real> &t, cudaStream_t s)
+cudaError_t run_stage2_any(const StageArgs &a, const Tables<Real> &t, cudaStream_t s, int *grid)
 {
     if (a.av_on) {
-        if (a.ns_on) return run_stage2<DIM, N, Real, true, true, TX, TY, TZ>(a, t, s);
-        return run_stage2<DIM, N, Real, true, false, TX, TY, TZ>(a, t, s);
+        if (a.ns_on) return run_stage2<DIM, N, Real, true, true, TX, TY, TZ>(a, t, s, grid);
+        return run_stage2<DIM, N, Real, true, false, TX, TY, TZ>(a, t, s, grid);
     }
-    if (a.ns_on) return run_stage2<DIM, N, Real, false, true, TX, TY, TZ>(a, t, s);
-    return run_stage2<DIM, N, Real, false, false, TX, TY, TZ>(a, t, s);
+    if (a.ns_on) return run_stage2<DIM, N, Real, false, true, TX, TY, TZ>(a, t, s, grid);
+    return run_stage2<DIM, N, Real, false, false, TX, TY, TZ>(a, t, s, grid);
 }
 
 }  // namespace dgx
