@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--impl", default="dgx", choices=["dgx", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-extras", action="store_true", help="skip the fp64 side run, e2e and cpu baseline")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the batched 64-member ensemble measurement")
     return ap.parse_args()
 
 
@@ -213,6 +214,61 @@ def reference_arm(args, rank, ws):
     print(json.dumps(line), flush=True)
 
 
+def rk_stages_for(n: int) -> int:
+    """default SSP-RK stage count of degree n (the library's choice when rk_stages is 0)"""
+    return {0: 1, 1: 2, 2: 3}.get(n, 5)
+
+
+def ensemble_measurement(dgx, inputs, torch, stream, steps: int, warmup: int):
+    """64 independent 2-D runs of mixed size (64..512 cells per axis), degree (1..5) and physics
+    (density wave / Sod tube, Euler+AV / NS+AV), FP32-bulk: whole SSP-RK steps of all members, batched
+    (one persistent stage kernel per (degree, physics) group over every member's tiles, per-member
+    device dt, CUDA graph) against the same members stepped one after another on the same stream.
+    Both are timed with CUDA events on that stream around `steps` whole steps."""
+    members = inputs.c5_manifest(count=64)
+    sims = []
+    for m in members:
+        s = dgx.Simulation(m.wl, precision=dgx.DG_FP32_BULK)
+        s.set_stream(stream)
+        s.set_state(inputs.member_state(m))
+        sims.append(s)
+    units = sum(m.wl.dofs * rk_stages_for(m.wl.n) for m in members)
+    state_bytes = sum(m.wl.nfields * m.wl.ncell * m.wl.M * (8 + 4) for m in members)  # u^n (FP64) + u_hi (FP32)
+    batch = dgx.dg_batch_create([s.h for s in sims])
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        fn(warmup)
+        torch.cuda.synchronize()
+        ev0.record()
+        fn(steps)
+        ev1.record()
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / steps
+
+    def batched(k):
+        dgx.dg_batch_step(batch, k)
+
+    def separate(k):
+        for _ in range(k):
+            for s in sims:
+                dgx.dg_step(s.h, 0.0)
+
+    ms_b = timed(batched)
+    ms_s = timed(separate)
+    dgx.dg_batch_sync(batch)
+    dgx.dg_batch_destroy(batch)
+    for s in sims:
+        s.close()
+    return {"workload": "ensemble_64_mixed_2d_deg1to5_fp32bulk", "members": len(members),
+            "cells_per_axis": sorted({m.wl.N[0] for m in members}),
+            "dof_updates_per_step": units, "state_bytes": state_bytes, "steps": steps, "warmup": warmup,
+            "batched": {"ms_per_step": ms_b, "value": units / (ms_b / 1e3), "unit": UNIT},
+            "one_by_one": {"ms_per_step": ms_s, "value": units / (ms_s / 1e3), "unit": UNIT},
+            "speedup": ms_s / ms_b,
+            "l2": "not flushed; the members' state alone exceeds L2"}
+
+
 def dgx_arm(args, rank, ws, local):
     import numpy as np
     import torch
@@ -327,6 +383,8 @@ def dgx_arm(args, rank, ws, local):
                                     "kind": "oracle",
                                     "sample": f"full 256x256 grid, {done} whole FP64 SSP(5,4) steps"}
     sim.close()
+    if not args.no_ensemble:
+        line["ensemble"] = ensemble_measurement(dgx, inputs, torch, stream, steps=20, warmup=3)
     if rank == 0:
         print(json.dumps(line), flush=True)
 

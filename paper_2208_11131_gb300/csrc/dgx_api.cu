@@ -7,8 +7,11 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <map>
 #include <new>
 #include <string>
+#include <tuple>
+#include <vector>
 
 #include "../../include/dgx.h"
 #include "dgx_internal.h"
@@ -138,6 +141,23 @@ __global__ void sums_final_kernel(const double *partial, int nblk, int nc, doubl
         double s = 0.0;
         for (int b = 0; b < nblk; ++b) s += partial[b * nc + threadIdx.x];
         out[threadIdx.x] = s * vol;
+    }
+}
+
+// per-simulation time step of a batch: from the CFL maxima the first stage accumulated in
+// descriptor.partial[0..1] (then reset for the next step), or a fixed dt
+__global__ void batch_dt_kernel(const StageArgs *d, int nsims, int P, double fixed_dt)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nsims; i += gridDim.x * blockDim.x) {
+        const StageArgs &a = d[i];
+        const double dt = fixed_dt > 0.0 ? fixed_dt : a.cfl * a.hmin / (2.0 * P * (a.partial[0] + a.partial[1]));
+        if (!(dt > 0.0) || !isfinite(dt)) atomicOr(a.status, DG_STATUS_BADDT);
+        double *dtp = const_cast<double *>(a.dtp);
+        dtp[0] = dt;
+        dtp[1] += 1.0;
+        dtp[2] += dt;
+        a.partial[0] = 0.0;
+        a.partial[1] = 0.0;
     }
 }
 
@@ -321,8 +341,10 @@ void base_stage_args(const dg_t *h, StageArgs &a)
     a.status = h->status;
 }
 
-cudaError_t launch_stage_any(const dg_t *h, const StageArgs &a, int *grid = nullptr)
+cudaError_t launch_stage_any(const dg_t *h, const StageArgs &a_in, int *grid = nullptr)
 {
+    StageArgs a = a_in;
+    stage_consts(a, h->degree, h->dim);
     if (h->dim == 2)
         return fp32(h) ? launch_stage_2d_f32(h->degree, a, h->tf, h->stream, grid)
                        : launch_stage_2d_f64(h->degree, a, h->td, h->stream, grid);
@@ -389,6 +411,45 @@ int prepare_kernels(dg_t *h)
 
 int stage_count(const dg_t *h) { return h->p.rk_stages > 0 ? h->p.rk_stages : auto_stages(h->degree); }
 
+// arguments of stage i of a step that starts from the state buffer `c` (u^n), with or without
+// the prologue folded into the first stage
+void fill_stage_args(const dg_t *h, const Schedule &S, int i, int c, bool fused, StageArgs &a)
+{
+    const StageDesc &d = S.s[i];
+    const int nx = 1 - c;
+    base_stage_args(h, a);
+    a.ubase = fp32(h) ? (const void *)h->Uhi[c] : (const void *)h->U[c];
+    a.din = d.in >= 0 ? h->D[d.in] : nullptr;
+    a.mode = d.last ? 2 : 1;
+    a.xbuf = d.x >= 0 ? h->D[d.x] : nullptr;
+    a.dout = d.out >= 0 ? h->D[d.out] : nullptr;
+    a.ca = d.ca;
+    a.cx = d.cx;
+    a.cb = d.cb;
+    a.za = d.za;
+    a.zx = d.zx;
+    a.zb = d.zb;
+    a.write_z = d.write_z;
+    a.uold = h->U[c];
+    a.unew = h->U[nx];
+    a.uhi_new = fp32(h) ? h->Uhi[nx] : nullptr;
+    a.cfl = h->p.cfl;
+    if (fused && i == 0) {
+        a.fused = 1;
+        a.partial = h->partial;
+        a.S_prev = h->Sprev;
+        a.wig_w = h->wig;
+        a.f_w = h->p.f_w;
+        a.s_on = h->p.s_onset / ((double)(h->degree + 1) * (h->degree + 1));
+        a.epi_unit_dt = 1;  // delta_1 := L(u^n); scaled by cb dt where it is read
+        a.cb = 1.0;
+    }
+    if (fused && i == 1) {
+        a.din_dt = 1;
+        a.din_coef = S.s[0].cb;
+    }
+}
+
 // enqueue one full step on h->stream (no host synchronisation).  With `ev`, an event is recorded
 // before the first launch (ev[0]) and after each launch in launch order (ev[1..]).
 //
@@ -427,36 +488,7 @@ int enqueue_step(dg_t *h, double dt, cudaEvent_t *ev = nullptr)
     for (int i = 0; i < S.stages; ++i) {
         const StageDesc &d = S.s[i];
         StageArgs a;
-        base_stage_args(h, a);
-        a.ubase = fp32(h) ? (const void *)h->Uhi[c] : (const void *)h->U[c];
-        a.din = d.in >= 0 ? h->D[d.in] : nullptr;
-        a.mode = d.last ? 2 : 1;
-        a.xbuf = d.x >= 0 ? h->D[d.x] : nullptr;
-        a.dout = d.out >= 0 ? h->D[d.out] : nullptr;
-        a.ca = d.ca;
-        a.cx = d.cx;
-        a.cb = d.cb;
-        a.za = d.za;
-        a.zx = d.zx;
-        a.zb = d.zb;
-        a.write_z = d.write_z;
-        a.uold = h->U[c];
-        a.unew = h->U[nx];
-        a.uhi_new = fp32(h) ? h->Uhi[nx] : nullptr;
-        if (fused && i == 0) {
-            a.fused = 1;
-            a.partial = h->partial;
-            a.S_prev = h->Sprev;
-            a.wig_w = h->wig;
-            a.f_w = h->p.f_w;
-            a.s_on = h->p.s_onset / ((double)(h->degree + 1) * (h->degree + 1));
-            a.epi_unit_dt = 1;  // delta_1 := L(u^n); scaled by cb dt where it is read
-            a.cb = 1.0;
-        }
-        if (fused && i == 1) {
-            a.din_dt = 1;
-            a.din_coef = S.s[0].cb;
-        }
+        fill_stage_args(h, S, i, c, fused, a);
         int grid = 0;
         CK(h, launch_stage_any(h, a, &grid));
         if (h->p.positivity_on) {
@@ -846,6 +878,255 @@ const char *dg_last_error(const dg_t *h)
 {
     if (!h) return "null handle";
     return h->err.c_str();
+}
+
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batched ensembles
+
+struct dg_batch {
+    struct Group {
+        int dim = 2, degree = 0, prec = 0, av = 0, ns = 0, stages = 0;
+        std::vector<int> members;
+        int total_tiles = 0;
+        StageArgs *d_desc = nullptr;  // [2 parities][stages][members]
+        int *d_off = nullptr;         // [members + 1] tile prefix sums
+        double *d_max = nullptr;      // [members][2] CFL maxima of the first stage
+        const dg_t *rep = nullptr;    // member that owns the group's operator tables
+        cudaStream_t st = nullptr;
+        cudaEvent_t done = nullptr;
+    };
+    std::vector<dg_t *> sims;
+    std::vector<Group> groups;
+    cudaStream_t stream = nullptr;  // stream of the members (the batch's origin stream)
+    cudaStream_t cap = nullptr;
+    cudaEvent_t fork = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    double graph_dt = 0.0;
+    int parity = 0;
+    std::string err;
+};
+
+namespace {
+
+int bfail(dg_batch_t *b, int code, const char *msg)
+{
+    if (b) b->err = msg;
+    return code;
+}
+
+// one batched stage launch of a group; prepare_only sets the kernel attributes without launching
+cudaError_t launch_batch_group(const dg_batch::Group &g, int parity, int i, cudaStream_t s, bool prepare_only = false)
+{
+    const StageArgs *d = g.d_desc + ((size_t)parity * g.stages + i) * g.members.size();
+    const int nm = (int)g.members.size();
+    const int tot = prepare_only ? 0 : g.total_tiles;
+    if (g.dim == 2)
+        return g.prec ? launch_stage_batch_2d_f32(g.degree, g.av, g.ns, d, g.d_off, nm, tot, g.rep->tf, s)
+                      : launch_stage_batch_2d_f64(g.degree, g.av, g.ns, d, g.d_off, nm, tot, g.rep->td, s);
+    return g.prec ? launch_stage_batch_3d_f32(g.degree, g.av, g.ns, d, g.d_off, nm, tot, g.rep->tf, s)
+                  : launch_stage_batch_3d_f64(g.degree, g.av, g.ns, d, g.d_off, nm, tot, g.rep->td, s);
+}
+
+// one step of every member: each group on its own stream, forked from and joined to `origin`
+int enqueue_batch_step(dg_batch_t *b, double dt, cudaStream_t origin)
+{
+    if (cudaEventRecord(b->fork, origin) != cudaSuccess) return bfail(b, DG_ECUDA, "cudaEventRecord");
+    for (auto &g : b->groups) {
+        if (cudaStreamWaitEvent(g.st, b->fork, 0) != cudaSuccess) return bfail(b, DG_ECUDA, "cudaStreamWaitEvent");
+        for (int i = 0; i < g.stages; ++i) {
+            if (launch_batch_group(g, b->parity, i, g.st) != cudaSuccess) return bfail(b, DG_ECUDA, "batched stage launch");
+            if (i == 0) {
+                const StageArgs *d = g.d_desc + (size_t)b->parity * g.stages * g.members.size();
+                batch_dt_kernel<<<1, 256, 0, g.st>>>(d, (int)g.members.size(), g.degree + 1, dt > 0.0 ? dt : 0.0);
+                if (cudaGetLastError() != cudaSuccess) return bfail(b, DG_ECUDA, "batched dt launch");
+            }
+        }
+        if (cudaEventRecord(g.done, g.st) != cudaSuccess) return bfail(b, DG_ECUDA, "cudaEventRecord");
+        if (cudaStreamWaitEvent(origin, g.done, 0) != cudaSuccess) return bfail(b, DG_ECUDA, "cudaStreamWaitEvent");
+    }
+    b->parity ^= 1;
+    for (dg_t *h : b->sims) h->cur ^= 1;
+    return DG_OK;
+}
+
+void free_batch(dg_batch_t *b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (auto &g : b->groups) {
+        cudaFree(g.d_desc);
+        cudaFree(g.d_off);
+        cudaFree(g.d_max);
+        if (g.st) cudaStreamDestroy(g.st);
+        if (g.done) cudaEventDestroy(g.done);
+    }
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->fork) cudaEventDestroy(b->fork);
+}
+
+}  // namespace
+
+extern "C" {
+
+int dg_batch_create(dg_t *const *sims, int count, dg_batch_t **out)
+{
+    if (!out || !sims || count < 1) return DG_EINVAL;
+    *out = nullptr;
+    for (int k = 0; k < count; ++k) {
+        const dg_t *h = sims[k];
+        if (!h) return DG_EINVAL;
+        if (h->p.positivity_on || stage_count(h) < 2) return DG_EUNSUPPORTED;
+        if (h->cur != sims[0]->cur || h->device != sims[0]->device || h->stream != sims[0]->stream)
+            return DG_EINVAL;
+    }
+    dg_batch_t *b = new (std::nothrow) dg_batch_t();
+    if (!b) return DG_ENOMEM;
+    b->sims.assign(sims, sims + count);
+    b->stream = sims[0]->stream;
+    b->parity = sims[0]->cur;
+    std::map<std::tuple<int, int, int, int, int>, int> key_to_group;
+    for (int k = 0; k < count; ++k) {
+        const dg_t *h = sims[k];
+        const int ns = (h->nu > 0.0 || h->kappa > 0.0) ? 1 : 0;
+        const auto key = std::make_tuple(h->dim, h->degree, (int)fp32(h), h->p.av_on, ns);
+        auto it = key_to_group.find(key);
+        if (it == key_to_group.end()) {
+            dg_batch::Group g;
+            g.dim = h->dim;
+            g.degree = h->degree;
+            g.prec = fp32(h) ? 1 : 0;
+            g.av = h->p.av_on;
+            g.ns = ns;
+            g.stages = stage_count(h);
+            g.rep = h;
+            it = key_to_group.emplace(key, (int)b->groups.size()).first;
+            b->groups.push_back(g);
+        }
+        b->groups[it->second].members.push_back(k);
+    }
+    int st = DG_OK;
+    for (auto &g : b->groups) {
+        const int nm = (int)g.members.size();
+        const Schedule S = schedule_for(g.stages);
+        std::vector<int> off(nm + 1, 0);
+        for (int m = 0; m < nm; ++m) {
+            const dg_t *h = sims[g.members[m]];
+            off[m + 1] = off[m] + h->sgrid[0] * h->sgrid[1] * h->sgrid[2];
+        }
+        g.total_tiles = off[nm];
+        if (cudaMalloc((void **)&g.d_off, sizeof(int) * (nm + 1)) != cudaSuccess ||
+            cudaMalloc((void **)&g.d_max, sizeof(double) * 2 * nm) != cudaSuccess ||
+            cudaMalloc((void **)&g.d_desc, sizeof(StageArgs) * 2 * g.stages * nm) != cudaSuccess) {
+            cudaGetLastError();
+            st = DG_ENOMEM;
+            break;
+        }
+        std::vector<StageArgs> host((size_t)2 * g.stages * nm);
+        for (int par = 0; par < 2; ++par)
+            for (int i = 0; i < g.stages; ++i)
+                for (int m = 0; m < nm; ++m) {
+                    StageArgs &a = host[((size_t)par * g.stages + i) * nm + m];
+                    fill_stage_args(sims[g.members[m]], S, i, par, true, a);
+                    if (i == 0) a.partial = g.d_max + 2 * m;  // per-simulation maxima (atomics)
+                    stage_consts(a, g.degree, g.dim);
+                }
+        if (cudaMemcpy(g.d_off, off.data(), sizeof(int) * (nm + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemset(g.d_max, 0, sizeof(double) * 2 * nm) != cudaSuccess ||
+            cudaMemcpy(g.d_desc, host.data(), sizeof(StageArgs) * host.size(), cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            cudaStreamCreateWithFlags(&g.st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            st = DG_ECUDA;
+            break;
+        }
+        // kernel attributes and occupancy, before any capture
+        if (launch_batch_group(g, 0, 0, g.st, true) != cudaSuccess) {
+            st = DG_ECUDA;
+            break;
+        }
+    }
+    if (!st && (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)) {
+        cudaGetLastError();
+        st = DG_ECUDA;
+    }
+    if (st) {
+        free_batch(b);
+        delete b;
+        return st;
+    }
+    *out = b;
+    return DG_OK;
+}
+
+int dg_batch_step(dg_batch_t *b, int nsteps, double dt)
+{
+    if (!b || nsteps < 0) return DG_EINVAL;
+    int done = 0;
+    if (b->parity != 0 && nsteps > 0) {
+        int st = enqueue_batch_step(b, dt, b->stream);
+        if (st) return st;
+        ++done;
+    }
+    if (nsteps - done >= 2) {
+        if (!b->graph || b->graph_dt != dt) {
+            if (b->graph) cudaGraphExecDestroy(b->graph);
+            b->graph = nullptr;
+            if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                return bfail(b, DG_ECUDA, "cudaStreamBeginCapture");
+            int st = enqueue_batch_step(b, dt, b->cap);
+            if (!st) st = enqueue_batch_step(b, dt, b->cap);
+            cudaGraph_t g = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+            if (st) {
+                if (g) cudaGraphDestroy(g);
+                return st;
+            }
+            if (e != cudaSuccess) return bfail(b, DG_ECUDA, "graph capture");
+            const cudaError_t ei = cudaGraphInstantiate(&b->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (ei != cudaSuccess) {
+                b->graph = nullptr;
+                return bfail(b, DG_ECUDA, "graph instantiate");
+            }
+            b->graph_dt = dt;
+        }
+        while (nsteps - done >= 2) {
+            if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess) return bfail(b, DG_ECUDA, "cudaGraphLaunch");
+            done += 2;
+        }
+    }
+    while (done < nsteps) {
+        int st = enqueue_batch_step(b, dt, b->stream);
+        if (st) return st;
+        ++done;
+    }
+    return DG_OK;
+}
+
+int dg_batch_sync(dg_batch_t *b)
+{
+    if (!b) return DG_EINVAL;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, DG_ECUDA, "cudaStreamSynchronize");
+    int worst = DG_OK;
+    for (dg_t *h : b->sims) {
+        const int st = check_status(h);
+        if (st && !worst) worst = st;
+    }
+    if (worst) b->err = "a member reported a non-physical state or time step";
+    return worst;
+}
+
+const char *dg_batch_last_error(const dg_batch_t *b) { return b ? b->err.c_str() : "null batch"; }
+
+void dg_batch_destroy(dg_batch_t *b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    free_batch(b);
+    delete b;
 }
 
 }  // extern "C"

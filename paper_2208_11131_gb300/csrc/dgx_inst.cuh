@@ -20,6 +20,9 @@ namespace dgx {
 #define DGX_PRO_CASE(n, sx, sy, sz, px, py, pz) \
     case n:                                     \
         return run_prologue<DGX_DIM, n, DGX_REAL, px, py, pz>(a, t, s);
+#define DGX_BATCH_CASE(n, sx, sy, sz, px, py, pz) \
+    case n:                                      \
+        return run_stage2_batch_any<DGX_DIM, n, DGX_REAL, sx, sy, sz>(av, ns, descs, tile_off, nsims, total, t, s);
 #define DGX_LIM_CASE(n, sx, sy, sz, px, py, pz) \
     case n:                                    \
         return run_limiter<DGX_DIM, n, DGX_REAL>(a, t, s);
@@ -44,6 +47,14 @@ cudaError_t DGX_CAT(launch_prologue_, DGX_SUFFIX)(int degree, const PrologueArgs
                                                   cudaStream_t s)
 {
     switch (degree) { DGX_TILES(DGX_PRO_CASE) }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t DGX_CAT(launch_stage_batch_, DGX_SUFFIX)(int degree, int av, int ns, const StageArgs *descs,
+                                                     const int *tile_off, int nsims, int total,
+                                                     const Tables<DGX_REAL> &t, cudaStream_t s)
+{
+    switch (degree) { DGX_TILES(DGX_BATCH_CASE) }
     return cudaErrorInvalidValue;
 }
 

@@ -37,6 +37,21 @@ struct Tables {
 void make_tables(int degree, Tables<double> *td, Tables<float> *tf);
 
 // Arguments of the fused right-hand-side / Runge-Kutta stage kernel.
+// indices of StageArgs::kf / kd
+enum StageConst {
+    SK_TWO_H = 0,   // 2 / h_a, a = 0..2
+    SK_INV_H = 3,   // 1 / h_a
+    SK_CAX = 6,     // face-integral weight of axis a over h_a (1/2 in 2-D, 1/4 in 3-D)
+    SK_EPS = 9,     // av_scale h_min / (n+1): AV viscosity per unit alpha c_s
+    SK_INV_TAU,     // (n+1) / (f_tau h_min): alpha decay rate per unit c_s
+    SK_FV,
+    SK_GAMMA,
+    SK_NU,
+    SK_KAPPA,
+    SK_CA, SK_CX, SK_CB, SK_ZA, SK_ZX, SK_ZB,  // Runge-Kutta register coefficients
+    SK_COUNT
+};
+
 struct StageArgs {
     int N[3];      // cells per axis (1 for unused axes)
     int bc[3];     // 0 periodic, 1 outflow
@@ -81,7 +96,42 @@ struct StageArgs {
     // true delta = din_coef * dtp[0] * din when din_dt is set
     int din_dt;
     double din_coef;
+    double cfl;  // CFL factor (read by the batched time-step kernel)
+
+    // per-simulation constants of the stage body in both precisions, derived on the host from the
+    // fields above by stage_consts() (FP64 divisions inside the tile loop are costly on this part)
+    float kf[SK_COUNT];
+    double kd[SK_COUNT];
 };
+
+static_assert(sizeof(StageArgs) % 8 == 0 && alignof(StageArgs) == 8, "StageArgs is copied as 8-byte words");
+
+// fill StageArgs::kf / kd (degree: polynomial degree, dim: 2 or 3); call after every other field is set
+inline void stage_consts(StageArgs &a, int degree, int dim)
+{
+    double k[SK_COUNT];
+    for (int i = 0; i < 3; ++i) {
+        k[SK_TWO_H + i] = 2.0 / a.h[i];
+        k[SK_INV_H + i] = 1.0 / a.h[i];
+        k[SK_CAX + i] = (dim == 2 ? 0.5 : 0.25) / a.h[i];
+    }
+    k[SK_EPS] = a.av_scale * a.hmin / (degree + 1);
+    k[SK_INV_TAU] = (degree + 1) / (a.f_tau * a.hmin);
+    k[SK_FV] = a.f_v;
+    k[SK_GAMMA] = a.gamma;
+    k[SK_NU] = a.nu;
+    k[SK_KAPPA] = a.kappa;
+    k[SK_CA] = a.ca;
+    k[SK_CX] = a.cx;
+    k[SK_CB] = a.cb;
+    k[SK_ZA] = a.za;
+    k[SK_ZX] = a.zx;
+    k[SK_ZB] = a.zb;
+    for (int i = 0; i < SK_COUNT; ++i) {
+        a.kd[i] = k[i];
+        a.kf[i] = (float)k[i];
+    }
+}
 
 // Arguments of the step-prologue kernel (CFL speeds + oscillation sensor).
 struct PrologueArgs {
@@ -138,6 +188,14 @@ cudaError_t launch_limiter_2d_f64(int degree, const LimiterArgs &a, const Tables
 cudaError_t launch_limiter_2d_f32(int degree, const LimiterArgs &a, const Tables<float> &t, cudaStream_t s);
 cudaError_t launch_limiter_3d_f64(int degree, const LimiterArgs &a, const Tables<double> &t, cudaStream_t s);
 cudaError_t launch_limiter_3d_f32(int degree, const LimiterArgs &a, const Tables<float> &t, cudaStream_t s);
+cudaError_t launch_stage_batch_2d_f64(int degree, int av, int ns, const StageArgs *descs, const int *tile_off,
+                                      int nsims, int total, const Tables<double> &t, cudaStream_t s);
+cudaError_t launch_stage_batch_2d_f32(int degree, int av, int ns, const StageArgs *descs, const int *tile_off,
+                                      int nsims, int total, const Tables<float> &t, cudaStream_t s);
+cudaError_t launch_stage_batch_3d_f64(int degree, int av, int ns, const StageArgs *descs, const int *tile_off,
+                                      int nsims, int total, const Tables<double> &t, cudaStream_t s);
+cudaError_t launch_stage_batch_3d_f32(int degree, int av, int ns, const StageArgs *descs, const int *tile_off,
+                                      int nsims, int total, const Tables<float> &t, cudaStream_t s);
 void tiles_2d_f64(int degree, int *stage, int *pro);
 void tiles_2d_f32(int degree, int *stage, int *pro);
 void tiles_3d_f64(int degree, int *stage, int *pro);

@@ -66,8 +66,12 @@ struct Stage2Plan {
     static constexpr int CHUNK = CELL_BYTES % 16 == 0 ? 16 : (CELL_BYTES % 8 == 0 ? 8 : 4);
 };
 
-template <int DIM, int N, typename Real, bool AV, bool NS, int TX, int TY, int TZ, bool PF>
-__global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Tables<Real> Tg)
+// Body shared by the single-simulation kernel (A0: its arguments) and the batched kernel (descs:
+// one argument set per simulation; tile_off: prefix sums of the simulations' tile counts, so the
+// work list is every (simulation, tile) pair in order).
+template <int DIM, int N, typename Real, bool AV, bool NS, int TX, int TY, int TZ, bool PF, bool BATCH>
+__device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs *descs, const int *tile_off,
+                                            int nsims, const Tables<Real> &Tg)
 {
     using S = Shape<DIM, N, TX, TY, TZ>;
     using PL = Stage2Plan<DIM, N, Real, AV, NS, TX, TY, TZ, PF>;
@@ -87,9 +91,20 @@ __global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Ta
     __shared__ int s_status;
 
     const int tid = threadIdx.x, nth = blockDim.x;
-    const int ntiles = A.ntile[0] * A.ntile[1] * A.ntile[2];
-    const Real *ub = static_cast<const Real *>(A.ubase);
-    const Real *di = static_cast<const Real *>(A.din);
+    const int ntiles = BATCH ? tile_off[nsims] : A0->ntile[0] * A0->ntile[1] * A0->ntile[2];
+    // simulation of a work-list tile (binary search in the prefix sums)
+    auto sim_of = [&](int tile) -> int {
+        if (!BATCH) return 0;
+        int lo = 0, hi = nsims - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tile_off[mid] <= tile) lo = mid;
+            else hi = mid - 1;
+        }
+        return lo;
+    };
+    auto args_of = [&](int sim) -> const StageArgs & { return BATCH ? descs[sim] : *A0; };
+    auto local_tile = [&](int tile, int sim) { return BATCH ? tile - tile_off[sim] : tile; };
 
     for (int i = tid; i < Q * Q; i += nth) {
         tB[i] = Tg.B[i / Q][i % Q];
@@ -107,26 +122,28 @@ __global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Ta
     }
     if (tid == 0) s_status = 0;
 
-    auto tile_origin = [&](int tile, int *o, int *V) {
+    auto tile_origin = [&](const StageArgs &T, int tile, int *o, int *V) {
         int b = tile;
-        const int tx = b % A.ntile[0];
-        b /= A.ntile[0];
-        const int ty = b % A.ntile[1];
-        const int tz = b / A.ntile[1];
+        const int tx = b % T.ntile[0];
+        b /= T.ntile[0];
+        const int ty = b % T.ntile[1];
+        const int tz = b / T.ntile[1];
         o[0] = tx * TX;
         o[1] = ty * TY;
         o[2] = tz * TZ;
-        V[0] = min(TX, A.N[0] - o[0]);
-        V[1] = min(TY, A.N[1] - o[1]);
-        V[2] = DIM == 3 ? min(TZ, A.N[2] - o[2]) : 1;
+        V[0] = min(TX, T.N[0] - o[0]);
+        V[1] = min(TY, T.N[1] - o[1]);
+        V[2] = DIM == 3 ? min(TZ, T.N[2] - o[2]) : 1;
     };
 
     // slot indices of a tile, then asynchronous copies of its stage state into sIn0 / sIn1
     // (called by all threads of the CTA)
-    auto issue_tile = [&](int tile, int *sG) {
+    auto issue_tile = [&](const StageArgs &T, int tile, int *sG) {
         int o[3], V[3];
-        tile_origin(tile, o, V);
-        for (int s = tid; s < NSLOT; s += nth) sG[s] = slot_global<S>(s, o, V, A.N, A.bc);
+        tile_origin(T, tile, o, V);
+        const Real *ub = static_cast<const Real *>(T.ubase);
+        const Real *di = static_cast<const Real *>(T.din);
+        for (int s = tid; s < NSLOT; s += nth) sG[s] = slot_global<S>(s, o, V, T.N, T.bc);
         __syncthreads();
         if constexpr (!PF) return;  // without prefetch buffers the tile is loaded at the top of its iteration
         constexpr int PER = PL::CELL_BYTES / PL::CHUNK;  // chunks per (field, cell)
@@ -137,7 +154,7 @@ __global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Ta
             const int slot = fs % NSLOT, f = fs / NSLOT;
             const int g = sG[slot];
             if (g < 0) continue;
-            const size_t gbyte = (((size_t)f * A.ncell + g) * NP) * sizeof(Real) + (size_t)c * PL::CHUNK;
+            const size_t gbyte = (((size_t)f * T.ncell + g) * NP) * sizeof(Real) + (size_t)c * PL::CHUNK;
             const size_t sbyte = ((size_t)(f * NSLOT + slot) * NP) * sizeof(Real) + (size_t)c * PL::CHUNK;
             const char *gu = reinterpret_cast<const char *>(ub) + gbyte;
             char *su = reinterpret_cast<char *>(sIn0) + sbyte;
@@ -155,37 +172,60 @@ __global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Ta
         cp_async_commit();
     };
 
-    const Real gamma = (Real)A.gamma, nu = (Real)A.nu, kappa = (Real)A.kappa;
-    const Real epsfac = (Real)(A.av_scale * A.hmin / (N + 1));
-    const Real inv_tau = (Real)((N + 1) / (A.f_tau * A.hmin));
-    const Real f_v = (Real)A.f_v;
-    const Real inv_f = Tg.inv_f;
-    Real two_h[3], cax[3], inv_h[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        two_h[a] = (Real)(2.0 / A.h[a]);
-        inv_h[a] = (Real)(1.0 / A.h[a]);
-        cax[a] = (Real)((DIM == 2 ? 0.5 : 0.25) / A.h[a]);
-    }
-    const Real src_w = (Real)(DIM == 2 ? 0.25 : 0.125);
-    const Real dt = A.epi_unit_dt ? Real(1) : ((A.mode != 0 && A.dtp) ? (Real)A.dtp[0] : Real(0));
-    const Real dsc = A.din_dt ? (Real)(A.din_coef * A.dtp[0]) : Real(1);  // stored delta -> true delta
     Real cmax = Real(0), vmax = Real(0);  // CFL speeds (fused first stage)
-    const Real ca = (Real)A.ca, cx = (Real)A.cx, cb = (Real)A.cb;
-    const Real za = (Real)A.za, zx = (Real)A.zx, zb = (Real)A.zb;
-    Real *xb = static_cast<Real *>(A.xbuf);
-    Real *dout = static_cast<Real *>(A.dout);
-    const bool readx = xb && (A.cx != 0.0 || A.zx != 0.0);
     int bad = 0;
 
     int tile = blockIdx.x;
     int *sG = sGa, *sGn = sGb;
     __syncthreads();
-    if (tile < ntiles) issue_tile(tile, sG);
+    if (tile < ntiles) {
+        const int sim = sim_of(tile);
+        issue_tile(args_of(sim), local_tile(tile, sim), sG);
+    }
 
+    // batched: the current simulation's arguments live in shared memory, so that the compiler need
+    // not reload them from global memory after every global store of the tile
+    __shared__ __align__(16) StageArgs s_desc;
+    int s_sim = -1;
     while (tile < ntiles) {
+        const int sim = sim_of(tile);
+        if constexpr (BATCH) {
+            if (sim != s_sim) {  // uniform over the CTA
+                __syncthreads();  // the previous tile's last reads of s_desc are done
+                const unsigned long long *src = reinterpret_cast<const unsigned long long *>(descs + sim);
+                unsigned long long *dst = reinterpret_cast<unsigned long long *>(&s_desc);
+                for (int i = tid; i < (int)(sizeof(StageArgs) / 8); i += nth) dst[i] = src[i];
+                __syncthreads();
+                s_sim = sim;
+            }
+        }
+        const StageArgs &A = BATCH ? s_desc : *A0;
         int o[3], V[3];
-        tile_origin(tile, o, V);
+        tile_origin(A, local_tile(tile, sim), o, V);
+        const Real *ub = static_cast<const Real *>(A.ubase);
+        const Real *di = static_cast<const Real *>(A.din);
+        const Real *K;
+        if constexpr (sizeof(Real) == 4) K = A.kf;
+        else K = A.kd;
+        const Real gamma = K[SK_GAMMA], nu = K[SK_NU], kappa = K[SK_KAPPA];
+        const Real epsfac = K[SK_EPS], inv_tau = K[SK_INV_TAU], f_v = K[SK_FV];
+        const Real inv_f = Tg.inv_f;
+        Real two_h[3], cax[3], inv_h[3];
+    #pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            two_h[a] = K[SK_TWO_H + a];
+            inv_h[a] = K[SK_INV_H + a];
+            cax[a] = K[SK_CAX + a];
+        }
+        const Real src_w = (Real)(DIM == 2 ? 0.25 : 0.125);
+        const Real dt = A.epi_unit_dt ? Real(1) : ((A.mode != 0 && A.dtp) ? (Real)A.dtp[0] : Real(0));
+        const Real dsc = A.din_dt ? (Real)(A.din_coef * A.dtp[0]) : Real(1);  // stored delta -> true delta
+        const Real ca = K[SK_CA], cx = K[SK_CX], cb = K[SK_CB];
+        const Real za = K[SK_ZA], zx = K[SK_ZX], zb = K[SK_ZB];
+        Real *xb = static_cast<Real *>(A.xbuf);
+        Real *dout = static_cast<Real *>(A.dout);
+        const bool readx = xb && (A.cx != 0.0 || A.zx != 0.0);
+
         if constexpr (PF) {
             cp_async_wait_all();
             __syncthreads();
@@ -258,7 +298,7 @@ __global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Ta
                 for (int i = 0; i < Q; ++i) {
                     Real acc = Real(0);
 #pragma unroll
-                    for (int m = 0; m < Q; ++m) acc = fma(tB[i * Q + m], w[m], acc);
+                    for (int m = 0; m < Q; ++m) acc = fma(Tg.B[i][m], w[m], acc);
                     sU[base + i] = acc;
                 }
             }
@@ -266,7 +306,10 @@ __global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Ta
         __syncthreads();
         // the input buffers are free: start streaming the next tile
         const int next = tile + gridDim.x;
-        if (PF && next < ntiles) issue_tile(next, sGn);
+        if (PF && next < ntiles) {
+            const int nsim = sim_of(next);
+            issue_tile(args_of(nsim), local_tile(next, nsim), sGn);
+        }
 
         // ---- passes B (y) and C (z) in place
 #pragma unroll
@@ -287,7 +330,7 @@ __global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Ta
                 for (int i = 0; i < Q; ++i) {
                     Real acc = Real(0);
 #pragma unroll
-                    for (int m = 0; m < Q; ++m) acc = fma(tB[i * Q + m], w[m], acc);
+                    for (int m = 0; m < Q; ++m) acc = fma(Tg.B[i][m], w[m], acc);
                     sU[base + i * Sa] = acc;
                 }
             }
@@ -395,7 +438,7 @@ __global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Ta
                         const Real *pr = sU + (f * NSLOT + sr) * NP + base;
                         Real acc = Real(0);
 #pragma unroll
-                        for (int m = 0; m < Q; ++m) acc = fma(tCm[m], pl[m * Sa], fma(tCp[m], pr[m * Sa], acc));
+                        for (int m = 0; m < Q; ++m) acc = fma(Tg.Cm[m], pl[m * Sa], fma(Tg.Cp[m], pr[m * Sa], acc));
                         sUt[(f * NFACE + S::FOFF(a) + fl) * NPF + k] = acc;
                     }
                 };
@@ -433,14 +476,14 @@ __global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Ta
             if (sG[sl] < 0 || sG[sr] < 0) {
                 const bool right_in = sG[sl] < 0;
                 const int si = right_in ? sr : sl;
-                const Real *Lx = right_in ? tLm : tLp;
+
                 Real u[NC], v[3], rho, pr_, cs;
 #pragma unroll
                 for (int f = 0; f < NC; ++f) {
                     const Real *q = sU + (f * NSLOT + si) * NP + base;
                     Real acc = Real(0);
 #pragma unroll
-                    for (int m = 0; m < Q; ++m) acc = fma(Lx[m], q[m * Sa], acc);
+                    for (int m = 0; m < Q; ++m) acc = fma(right_in ? Tg.Lm[m] : Tg.Lp[m], q[m * Sa], acc);
                     u[f] = acc;
                 }
                 if (!primitives<DIM>(u, gamma, rho, v, pr_, cs)) bad = 1;
@@ -454,8 +497,8 @@ __global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Ta
                     Real al = Real(0), ar = Real(0);
 #pragma unroll
                     for (int m = 0; m < Q; ++m) {
-                        al = fma(tLp[m], ql[m * Sa], al);
-                        ar = fma(tLm[m], qr[m * Sa], ar);
+                        al = fma(Tg.Lp[m], ql[m * Sa], al);
+                        ar = fma(Tg.Lm[m], qr[m * Sa], ar);
                     }
                     uL[f] = al;
                     uR[f] = ar;
@@ -471,7 +514,7 @@ __global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Ta
                         const Real *qr = sU + (f * NSLOT + sr) * NP + base;
                         Real acc = Real(0);
 #pragma unroll
-                        for (int m = 0; m < Q; ++m) acc = fma(tDm[m], ql[m * Sa], fma(tDp[m], qr[m * Sa], acc));
+                        for (int m = 0; m < Q; ++m) acc = fma(Tg.Dm[m], ql[m * Sa], fma(Tg.Dp[m], qr[m * Sa], acc));
                         dn[f] = acc * sc;
                     }
                     if (NS) {
@@ -566,7 +609,7 @@ __global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Ta
                 for (int l = 0; l < Q; ++l) {
                     Real acc = Real(0);
 #pragma unroll
-                    for (int i = 0; i < Q; ++i) acc = fma(tB[i * Q + l], w[i], acc);
+                    for (int i = 0; i < Q; ++i) acc = fma(Tg.B[i][l], w[i], acc);
                     sR[base + l * Sa] = acc;
                 }
             }
@@ -590,7 +633,7 @@ __global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Ta
                 for (int l = 0; l < Q; ++l) {
                     Real acc = Real(0);
 #pragma unroll
-                    for (int i = 0; i < Q; ++i) acc = fma(tB[i * Q + l], w[i], acc);
+                    for (int i = 0; i < Q; ++i) acc = fma(Tg.B[i][l], w[i], acc);
                     L[l] = acc;
                 }
                 const size_t gi = ((size_t)f * A.ncell + g) * NP + (size_t)r * Q;
@@ -622,11 +665,35 @@ __global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Ta
             sG = sGn;
             sGn = t;
         } else if (next < ntiles) {
-            issue_tile(next, sG);  // slot map of the next tile (loaded at the top of the loop)
+            const int nsim = sim_of(next);
+            issue_tile(args_of(nsim), local_tile(next, nsim), sG);  // slot map of the next tile
+        }
+        if (BATCH) {
+            // per-simulation results of this tile: CFL maxima (fused first stage) and status
+            if (A.fused) {
+                double c = (double)cmax, v = (double)vmax;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    c = fmax(c, __shfl_xor_sync(0xffffffffu, c, off));
+                    v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+                }
+                if ((tid & 31) == 0) {
+                    // non-negative doubles order like their bit patterns
+                    atomicMax(reinterpret_cast<unsigned long long *>(A.partial), (unsigned long long)__double_as_longlong(c));
+                    atomicMax(reinterpret_cast<unsigned long long *>(A.partial + 1), (unsigned long long)__double_as_longlong(v));
+                }
+                cmax = vmax = Real(0);
+            }
+            if (bad) {
+                atomicOr(A.status, DG_STATUS_NONPHYS);
+                bad = 0;
+            }
         }
         tile = next;
     }
     cp_async_wait_all();
+    if (BATCH) return;
+    const StageArgs &A = *A0;
     if (bad) s_status = 1;
     if (A.fused) {
         double c = (double)cmax, v = (double)vmax;
@@ -651,6 +718,19 @@ __global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Ta
         A.partial[2 * blockIdx.x + 0] = c;
         A.partial[2 * blockIdx.x + 1] = v;
     }
+}
+
+template <int DIM, int N, typename Real, bool AV, bool NS, int TX, int TY, int TZ, bool PF>
+__global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Tables<Real> Tg)
+{
+    stage2_body<DIM, N, Real, AV, NS, TX, TY, TZ, PF, false>(&A, nullptr, nullptr, 1, Tg);
+}
+
+template <int DIM, int N, typename Real, bool AV, bool NS, int TX, int TY, int TZ, bool PF>
+__global__ void __launch_bounds__(256)
+    stage2_batch_kernel(const StageArgs *descs, const int *tile_off, int nsims, const Tables<Real> Tg)
+{
+    stage2_body<DIM, N, Real, AV, NS, TX, TY, TZ, PF, true>(nullptr, descs, tile_off, nsims, Tg);
 }
 
 template <int DIM, int N, typename Real, bool AV, bool NS, int TX, int TY, int TZ>
@@ -681,6 +761,46 @@ cudaError_t run_stage2(const StageArgs &a, const Tables<Real> &t, cudaStream_t s
     if (grid_out) *grid_out = grid;
     k<<<grid, 256, PL::BYTES, s>>>(a, t);
     return cudaGetLastError();
+}
+
+// batched launch: one persistent grid over the (simulation, tile) work list of a group
+template <int DIM, int N, typename Real, bool AV, bool NS, int TX, int TY, int TZ>
+cudaError_t run_stage2_batch(const StageArgs *descs, const int *tile_off, int nsims, int total_tiles,
+                             const Tables<Real> &t, cudaStream_t s)
+{
+    constexpr bool PF = Stage2Plan<DIM, N, Real, AV, NS, TX, TY, TZ, true>::BYTES <= 227 * 1024;
+    using PL = Stage2Plan<DIM, N, Real, AV, NS, TX, TY, TZ, PF>;
+    auto k = stage2_batch_kernel<DIM, N, Real, AV, NS, TX, TY, TZ, PF>;
+    static int blocks_per_sm = 0;
+    static int sms = 0;
+    if (!blocks_per_sm) {  // first call comes from the batch set-up, never from a graph capture
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::BYTES);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k, 256, PL::BYTES);
+        if (e != cudaSuccess) return e;
+        if (blocks_per_sm < 1) blocks_per_sm = 1;
+    }
+    if (total_tiles == 0) return cudaSuccess;
+    const int grid = total_tiles < sms * blocks_per_sm ? total_tiles : sms * blocks_per_sm;
+    k<<<grid, 256, PL::BYTES, s>>>(descs, tile_off, nsims, t);
+    return cudaGetLastError();
+}
+
+template <int DIM, int N, typename Real, int TX, int TY, int TZ>
+cudaError_t run_stage2_batch_any(int av, int ns, const StageArgs *descs, const int *tile_off, int nsims,
+                                 int total_tiles, const Tables<Real> &t, cudaStream_t s)
+{
+    if (av) {
+        if (ns) return run_stage2_batch<DIM, N, Real, true, true, TX, TY, TZ>(descs, tile_off, nsims, total_tiles, t, s);
+        return run_stage2_batch<DIM, N, Real, true, false, TX, TY, TZ>(descs, tile_off, nsims, total_tiles, t, s);
+    }
+    if (ns) return run_stage2_batch<DIM, N, Real, false, true, TX, TY, TZ>(descs, tile_off, nsims, total_tiles, t, s);
+    return run_stage2_batch<DIM, N, Real, false, false, TX, TY, TZ>(descs, tile_off, nsims, total_tiles, t, s);
 }
 
 // run-time (AV, NS) dispatch onto the compile-time variants

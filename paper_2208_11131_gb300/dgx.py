@@ -28,6 +28,7 @@ EXPORTS = (
     "dg_set_stream", "dg_set_state", "dg_get_state", "dg_set_state_device", "dg_get_state_device",
     "dg_rhs", "dg_rhs_device", "dg_step", "dg_steps", "dg_step_timed", "dg_sync", "dg_max_dt", "dg_conserved_sums",
     "dg_get_aux", "dg_set_aux", "dg_last_error", "dg_status_string", "dg_max_dt_noalloc",
+    "dg_batch_create", "dg_batch_step", "dg_batch_sync", "dg_batch_last_error", "dg_batch_destroy",
 )
 
 
@@ -80,6 +81,9 @@ def lib(path: str = LIB_PATH):
         "dg_sync": (I, [H]), "dg_max_dt": (I, [H, P]), "dg_conserved_sums": (I, [H, P]),
         "dg_get_aux": (I, [H, P, P, P]), "dg_set_aux": (I, [H, P, P, P]),
         "dg_last_error": (ctypes.c_char_p, [H]), "dg_status_string": (ctypes.c_char_p, [I]),
+        "dg_batch_create": (I, [ctypes.POINTER(H), I, ctypes.POINTER(H)]),
+        "dg_batch_step": (I, [H, I, ctypes.c_double]), "dg_batch_sync": (I, [H]),
+        "dg_batch_last_error": (ctypes.c_char_p, [H]), "dg_batch_destroy": (None, [H]),
         "dg_max_dt_noalloc": (I, [ctypes.POINTER(dg_grid), I, ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_void_p]),
     }
@@ -218,6 +222,31 @@ def dg_max_dt_noalloc(grid: dg_grid, degree: int, gamma: float, cfl: float, dev_
                                    ctypes.c_void_p(dev_state_ptr), ctypes.c_void_p(dev_dt_ptr),
                                    ctypes.c_void_p(stream_ptr))
     _check(None, code)
+
+
+def _bcheck(b, code):
+    if code != DG_OK:
+        msg = lib().dg_batch_last_error(b).decode() if b else lib().dg_status_string(code).decode()
+        raise DGError(code, msg or lib().dg_status_string(code).decode())
+
+
+def dg_batch_create(handles):
+    arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    b = ctypes.c_void_p()
+    _bcheck(None, lib().dg_batch_create(arr, len(handles), ctypes.byref(b)))
+    return b
+
+
+def dg_batch_step(b, nsteps: int, dt: float = 0.0):
+    _bcheck(b, lib().dg_batch_step(b, int(nsteps), float(dt)))
+
+
+def dg_batch_sync(b):
+    _bcheck(b, lib().dg_batch_sync(b))
+
+
+def dg_batch_destroy(b):
+    lib().dg_batch_destroy(b)
 
 
 # ---------------------------------------------------------------- convenience wrapper

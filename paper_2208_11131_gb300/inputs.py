@@ -230,3 +230,87 @@ def random_modal_state(wl: Workload, seed: int, amp: float = 0.05, decay: float 
     hi = rng.uniform(-1, 1, (wl.nfields, K, wl.M)) * scale[None, None, :] * amp
     w += hi * np.abs(mean)[:, :, None].clip(min=0.2)
     return np.ascontiguousarray(w)
+
+
+# ------------------------------------------------------------------ batched ensemble (64 uneven 2-D runs)
+
+def _proj1d(n: int, N: int, lo: float, hi: float, func, q: int | None = None) -> np.ndarray:
+    """[N, n+1] coefficients of the 1-D projection of func onto Pt_l in each of N equal cells."""
+    q = n + 3 if q is None else q
+    x, g = npleg.leggauss(q)
+    B = _pt_table(n, x)  # [q, n+1]
+    h = (hi - lo) / N
+    xc = lo + (np.arange(N) + 0.5) * h
+    X = xc[:, None] + 0.5 * h * x[None, :]
+    return 0.5 * np.einsum("kj,j,jl->kl", func(X), g, B)
+
+
+def _outer2d(A: np.ndarray, Bm: np.ndarray) -> np.ndarray:
+    """2-D modes from per-axis factors: w[iy*Nx+ix][lx + Q ly] = A[ix][lx] B[iy][ly]."""
+    Nx, Q = A.shape
+    Ny = Bm.shape[0]
+    w = np.einsum("xa,yb->yxba", A, Bm)  # [iy][ix][ly][lx]
+    return w.reshape(Ny * Nx, Q * Q)
+
+
+@dataclass(frozen=True)
+class Member:
+    wl: Workload
+    kind: str  # "wave" or "sod"
+    axis: int  # shock-tube axis
+
+
+def c5_manifest(seed: int = BASE_SEED, count: int = 64):
+    """64 independent 2-D runs: cells per axis drawn from {64,128,256,512} (log-uniform), degree
+    uniform in 1..5, half smooth density waves (periodic) and half Sod tubes along a seeded axis
+    (outflow along it), half of all members with NS (nu = kappa = 1e-4); AV on for all."""
+    rng = np.random.default_rng(seed + 5)
+    out = []
+    for i in range(count):
+        N = int(2 ** rng.integers(6, 10))
+        n = int(rng.integers(1, 6))
+        kind = "wave" if rng.random() < 0.5 else "sod"
+        axis = int(rng.integers(0, 2))
+        ns = rng.random() < 0.5
+        bc = (0, 0, 0)
+        gamma = 5.0 / 3.0
+        if kind == "sod":
+            bc = (1, 0, 0) if axis == 0 else (0, 1, 0)
+            gamma = 1.4
+        nu = 1e-4 if ns else 0.0
+        wl = Workload(f"member{i}", 2, n, (N, N, 1), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), bc=bc, gamma=gamma, nu=nu,
+                      kappa=nu, av_on=1, cfl=0.3, steps=50)
+        out.append(Member(wl, kind, axis))
+    return out
+
+
+def member_state(m: Member) -> np.ndarray:
+    """initial modes of an ensemble member by separable projection (exact for these initial states)"""
+    wl = m.wl
+    n, N = wl.n, wl.N[0]
+    Q = n + 1
+    w = np.zeros(wl.shape())
+    if m.kind == "wave":
+        # rho = 1 + 0.2 sin 2pi(x+y) = 1 + 0.2 (sin 2pi x cos 2pi y + cos 2pi x sin 2pi y); v = (1,1); p = 1
+        Sx = _proj1d(n, N, 0.0, 1.0, lambda X: np.sin(2 * np.pi * X))
+        Cx = _proj1d(n, N, 0.0, 1.0, lambda X: np.cos(2 * np.pi * X))
+        rho = 0.2 * (_outer2d(Sx, Cx) + _outer2d(Cx, Sx))
+        rho[:, 0] += 1.0
+        w[0] = rho
+        w[1] = rho
+        w[2] = rho
+        w[3] = rho
+        w[3][:, 0] += 1.0 / (wl.gamma - 1.0)
+    else:
+        step = lambda lo_v, hi_v: (lambda X: np.where(X < 0.5, lo_v, hi_v))
+        r1 = _proj1d(n, N, 0.0, 1.0, step(1.0, 0.125))
+        p1 = _proj1d(n, N, 0.0, 1.0, step(1.0, 0.1))
+        one = np.zeros((N, Q))
+        one[:, 0] = 1.0
+        if m.axis == 0:
+            w[0] = _outer2d(r1, one)
+            w[3] = _outer2d(p1, one) / (wl.gamma - 1.0)
+        else:
+            w[0] = _outer2d(one, r1)
+            w[3] = _outer2d(one, p1) / (wl.gamma - 1.0)
+    return np.ascontiguousarray(w)

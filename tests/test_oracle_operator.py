@@ -182,3 +182,16 @@ def test_inputs_projection_matches_oracle_projection():
     a = inputs.project(wl, inputs.shear_layer_ic(wl))
     b = oracle.project(P, inputs.shear_layer_ic(wl))
     assert np.abs(a - b).max() < 1e-13
+
+
+def test_ensemble_separable_projection_matches_full_projection():
+    """the fast separable projection of the ensemble's initial states equals the full 2-D projection"""
+    for m in inputs.c5_manifest(count=6):
+        wl = m.wl.with_(N=(8, 8, 1))
+        mm = inputs.Member(wl, m.kind, m.axis)
+        P = oracle.Problem(dim=2, n=wl.n, N=(8, 8), gamma=wl.gamma, av_on=1)
+        if m.kind == "wave":
+            ref = oracle.project(P, inputs.density_wave_ic(wl, 0.0))
+        else:
+            ref = oracle.project(P, inputs.sod_tube_ic(wl, axis=m.axis))
+        assert np.abs(inputs.member_state(mm) - ref).max() < 1e-13
