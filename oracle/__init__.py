@@ -54,7 +54,12 @@ class Cfg(ctypes.Structure):
         ("av_on", ctypes.c_int), ("av_scale", ctypes.c_double), ("f_v", ctypes.c_double),
         ("f_tau", ctypes.c_double), ("f_w", ctypes.c_double), ("s_onset", ctypes.c_double),
         ("positivity_on", ctypes.c_int), ("cfl", ctypes.c_double), ("rk_stages", ctypes.c_int),
+        ("forcing_on", ctypes.c_int), ("force_amp", ctypes.c_double), ("force_ts", ctypes.c_double),
+        ("force_dt", ctypes.c_double), ("force_seed", ctypes.c_ulonglong),
     ]
+
+FMODES = 16  # forcing-state mode stride
+FSTATE = 1 + 6 * FMODES
 
 
 _lib = None
@@ -78,6 +83,11 @@ def lib():
             "or_step": (I, [C, P, P, P, P, D, P]), "or_basis_eval": (I, [I, I, I, P, P]),
             "or_num_threads": (I, []), "or_set_num_threads": (None, [I]),
             "or_face_recovery": (I, [C, P, ctypes.c_long, ctypes.c_long, I, P, P]),
+            "or_rhs_forced": (I, [C, P, P, P, P]), "or_step_forced": (I, [C, P, P, P, P, P, D, P]),
+            "or_forcing_modes": (I, [I, ctypes.POINTER(ctypes.c_int)]),
+            "or_forcing_uniform": (D, [ctypes.c_ulonglong, ctypes.c_ulonglong]),
+            "or_forcing_normal": (D, [ctypes.c_ulonglong, ctypes.c_ulonglong]),
+            "or_forcing_update": (I, [C, P, D]), "or_forcing_eval": (I, [C, P, I, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -186,6 +196,11 @@ class Problem:
     positivity_on: int = 0
     cfl: float = 0.5
     rk_stages: int = 0
+    forcing_on: int = 0
+    force_amp: float = 0.0
+    force_ts: float = 1.0
+    force_dt: float = 0.01
+    force_seed: int = 0
 
     def cfg(self) -> Cfg:
         c = Cfg()
@@ -200,6 +215,9 @@ class Problem:
         c.av_on, c.av_scale, c.f_v, c.f_tau, c.f_w, c.s_onset = (int(self.av_on), self.av_scale, self.f_v,
                                                                 self.f_tau, self.f_w, self.s_onset)
         c.positivity_on, c.cfl, c.rk_stages = int(self.positivity_on), self.cfl, int(self.rk_stages)
+        c.forcing_on, c.force_amp, c.force_ts, c.force_dt = (int(self.forcing_on), self.force_amp, self.force_ts,
+                                                             self.force_dt)
+        c.force_seed = int(self.force_seed) & 0xFFFFFFFFFFFFFFFF
         return c
 
     @property
@@ -275,13 +293,56 @@ def l1_error(prob: Problem, w: np.ndarray, func, field: int = 0, q: int | None =
 
 # ---------------------------------------------------------------- operator calls
 
-def rhs(prob: Problem, w: np.ndarray, wig: np.ndarray | None = None):
+def rhs(prob: Problem, w: np.ndarray, wig: np.ndarray | None = None, fst: np.ndarray | None = None):
+    """dw/dt; with forcing on, ``fst`` is the forcing state whose driving field is added."""
     c = prob.cfg()
     w = np.ascontiguousarray(w, dtype=np.float64)
     out = np.zeros_like(w)
     wp = _p(np.ascontiguousarray(wig, dtype=np.float64)) if wig is not None else None
-    st = lib().or_rhs(ctypes.byref(c), _p(w), wp, _p(out))
+    fp = _p(np.ascontiguousarray(fst, dtype=np.float64)) if fst is not None else None
+    st = lib().or_rhs_forced(ctypes.byref(c), _p(w), wp, fp, _p(out))
     return out, st
+
+
+# ---------------------------------------------------------------- turbulence driving (Sec. 6)
+
+def forcing_modes(dim: int) -> np.ndarray:
+    """[nmodes, 3] integer wave vectors of the driving (one of every +-k pair)."""
+    k = (ctypes.c_int * (3 * FMODES))()
+    n = lib().or_forcing_modes(dim, k)
+    return np.array(k[: 3 * n], dtype=int).reshape(n, 3)
+
+
+def forcing_uniform(seed: int, i: int) -> float:
+    return lib().or_forcing_uniform(seed & 0xFFFFFFFFFFFFFFFF, i)
+
+
+def forcing_normal(seed: int, c: int) -> float:
+    return lib().or_forcing_normal(seed & 0xFFFFFFFFFFFFFFFF, c)
+
+
+def forcing_state() -> np.ndarray:
+    """a fresh forcing state: no update applied yet"""
+    f = np.zeros(FSTATE)
+    f[0] = -1.0
+    return f
+
+
+def forcing_update(prob: Problem, fst: np.ndarray, t: float) -> int:
+    """in place: apply every OU update due at time t"""
+    c = prob.cfg()
+    return lib().or_forcing_update(ctypes.byref(c), _p(fst), float(t))
+
+
+def forcing_eval(prob: Problem, fst: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """driving acceleration at physical points X [npts, dim] -> [npts, 3]"""
+    c = prob.cfg()
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    out = np.zeros((X.shape[0], 3))
+    st = lib().or_forcing_eval(ctypes.byref(c), _p(np.ascontiguousarray(fst)), X.shape[0], _p(X), _p(out))
+    if st != OK:
+        raise ValueError(st)
+    return out
 
 
 def face_recovery(prob: Problem, w: np.ndarray, KL: int, KR: int, axis: int):
@@ -333,9 +394,12 @@ class Sim:
     S_prev: np.ndarray = None
     wig: np.ndarray = None
     scal: np.ndarray = field(default_factory=lambda: np.zeros(3))  # dt_prev, step, t
+    fst: np.ndarray = None  # forcing state (Sec. 6 driving)
 
     def __post_init__(self):
         self.w = np.ascontiguousarray(self.w, dtype=np.float64).copy()
+        if self.fst is None:
+            self.fst = forcing_state()
         if self.S_prev is None:
             self.S_prev = np.zeros(self.prob.ncell)
         if self.wig is None:
@@ -344,8 +408,8 @@ class Sim:
     def step(self, dt: float = 0.0):
         c = self.prob.cfg()
         used = ctypes.c_double()
-        st = lib().or_step(ctypes.byref(c), _p(self.w), _p(self.S_prev), _p(self.wig), _p(self.scal), float(dt),
-                           ctypes.byref(used))
+        st = lib().or_step_forced(ctypes.byref(c), _p(self.w), _p(self.S_prev), _p(self.wig), _p(self.scal),
+                                  _p(self.fst), float(dt), ctypes.byref(used))
         return used.value, st
 
     @property

@@ -53,6 +53,7 @@
  *    crosses the boundary.
  */
 #include <math.h>
+#include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -80,6 +81,11 @@ typedef struct {
     int positivity_on;
     double cfl;
     int rk_stages; /* 0: automatic choice from the order */
+    /* turbulence driving (Sec. 6, "Driving"): amplitude of the |k| = 1 modes, OU correlation
+     * time t_s, update interval, generator seed */
+    int forcing_on;
+    double force_amp, force_ts, force_dt;
+    unsigned long long force_seed;
 } or_cfg;
 
 /* ------------------------------------------------------------------ */
@@ -503,6 +509,137 @@ static int check_cfg(const or_cfg *c)
     for (int a = 0; a < c->dim; ++a)
         if (c->N[a] < 1 || !(c->hi[a] > c->lo[a])) return OR_EINVAL;
     if (!(c->gamma > 1.0)) return OR_EINVAL;
+    if (c->forcing_on && (!(c->force_ts > 0.0) || !(c->force_dt > 0.0) || !(c->force_amp >= 0.0)))
+        return OR_EINVAL;
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Turbulence driving (Sec. 6, "Driving")                              */
+/* ------------------------------------------------------------------ */
+/* The acceleration field is a sum of Fourier modes with wave numbers 2pi/L <= |k| <= 2 (2pi/L),
+ * amplitude proportional to |k|^(-5/3), whose complex vector coefficients follow independent
+ * Ornstein-Uhlenbeck processes (correlation time t_s, advanced exactly at update instants
+ * j * force_dt) and are projected onto the plane normal to k (solenoidal driving, the
+ * projection equation of Sec. 6).  A real field needs one mode of every +-k pair:
+ *   s(x) = sum_m  Re(s_m) cos(K_m.(x-lo)) - Im(s_m) sin(K_m.(x-lo)),
+ *   s_m = A |k_m|^(-5/3) P(K_m) (X_m + i Y_m),  P(K) = I - K K^T / |K|^2,
+ * K_m,a = 2 pi k_m,a / L_a, |k_m| in units of 2 pi / L.  X_m, Y_m are unit-variance OU
+ * vectors (d components each).  Forcing state: fst[0] = index of the last update applied
+ * (-1: none yet), fst[1 + 6 m + q] = component q of (X_m, Y_m) (q = 0..2 real, 3..5 imaginary;
+ * components beyond d stay zero).
+ * Random numbers: the SplitMix64 generator (Steele, Lea & Flood 2014) used counter-based,
+ * output i of seed s is mix(s + (i+1) * 0x9E3779B97F4A7C15), mapped to (0,1) with 53 bits,
+ * and the Box-Muller transform (1958) of outputs 2c and 2c+1 for the normal draw of counter c;
+ * counter of (update j, mode m, component q) is (16 j + m) * 6 + q. */
+
+#define OR_FMODES 16 /* mode stride: the 3-D count; 2-D has 6 */
+#define OR_FSTATE (1 + 6 * OR_FMODES)
+
+static const double OR_PI = 3.14159265358979323846;
+
+/* wave vectors with 1 <= |k|^2 <= 4 whose first non-zero component is positive,
+ * in loop order kz (outer), ky, kx (inner); returns their count */
+int or_forcing_modes(int d, int *k)
+{
+    int n = 0;
+    int zr = d == 3 ? 2 : 0;
+    for (int kz = -zr; kz <= zr; ++kz)
+        for (int ky = -2; ky <= 2; ++ky)
+            for (int kx = -2; kx <= 2; ++kx) {
+                int k2 = kx * kx + ky * ky + kz * kz;
+                if (k2 < 1 || k2 > 4) continue;
+                int first = kx != 0 ? kx : (ky != 0 ? ky : kz);
+                if (first < 0) continue;
+                k[3 * n + 0] = kx;
+                k[3 * n + 1] = ky;
+                k[3 * n + 2] = kz;
+                ++n;
+            }
+    return n;
+}
+
+static uint64_t splitmix64_at(uint64_t seed, uint64_t i)
+{
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+double or_forcing_uniform(unsigned long long seed, unsigned long long i)
+{
+    return ((double)(splitmix64_at(seed, i) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+}
+
+double or_forcing_normal(unsigned long long seed, unsigned long long c)
+{
+    double u1 = or_forcing_uniform(seed, 2 * c), u2 = or_forcing_uniform(seed, 2 * c + 1);
+    return sqrt(-2.0 * log(u1)) * cos(2.0 * OR_PI * u2);
+}
+
+/* apply every OU update due at time t (update j at time j * force_dt; j = 0 draws the
+ * stationary initial state) */
+int or_forcing_update(const or_cfg *c, double *fst, double t)
+{
+    if (check_cfg(c) || !c->forcing_on) return OR_EINVAL;
+    int k[3 * OR_FMODES];
+    int nm = or_forcing_modes(c->dim, k);
+    double f = exp(-c->force_dt / c->force_ts), g = sqrt(1.0 - f * f);
+    long j = (long)fst[0];
+    if (fst[0] < 0.0) {
+        j = 0;
+        for (int m = 0; m < nm; ++m)
+            for (int q = 0; q < 6; ++q)
+                fst[1 + 6 * m + q] = (q % 3) < c->dim ? or_forcing_normal(c->force_seed, (uint64_t)m * 6 + q) : 0.0;
+    }
+    long count = 0;
+    while ((double)(j + 1) * c->force_dt <= t) {
+        if (++count > 10000000L) return OR_EINVAL;
+        ++j;
+        for (int m = 0; m < nm; ++m)
+            for (int q = 0; q < 6; ++q) {
+                if ((q % 3) >= c->dim) continue;
+                double xi = or_forcing_normal(c->force_seed, ((uint64_t)j * OR_FMODES + m) * 6 + q);
+                fst[1 + 6 * m + q] = f * fst[1 + 6 * m + q] + g * xi;
+            }
+    }
+    fst[0] = (double)j;
+    return OR_OK;
+}
+
+/* driving acceleration at physical points x[npts][d] -> s[npts][3] */
+int or_forcing_eval(const or_cfg *c, const double *fst, int npts, const double *x, double *s)
+{
+    if (check_cfg(c)) return OR_EINVAL;
+    int d = c->dim;
+    int k[3 * OR_FMODES];
+    int nm = or_forcing_modes(d, k);
+    for (int i = 0; i < npts; ++i) {
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int m = 0; m < nm; ++m) {
+            double K[3] = {0.0, 0.0, 0.0}, K2 = 0.0, kk = 0.0, ph = 0.0;
+            for (int a = 0; a < d; ++a) {
+                K[a] = 2.0 * OR_PI * k[3 * m + a] / (c->hi[a] - c->lo[a]);
+                K2 += K[a] * K[a];
+                kk += (double)k[3 * m + a] * k[3 * m + a];
+                ph += K[a] * (x[i * d + a] - c->lo[a]);
+            }
+            double amp = c->force_amp * pow(sqrt(kk), -5.0 / 3.0);
+            const double *X = fst + 1 + 6 * m, *Y = X + 3;
+            double KX = 0.0, KY = 0.0;
+            for (int a = 0; a < d; ++a) {
+                KX += K[a] * X[a];
+                KY += K[a] * Y[a];
+            }
+            double cs = cos(ph), sn = sin(ph);
+            for (int a = 0; a < d; ++a) {
+                double re = X[a] - K[a] * KX / K2, im = Y[a] - K[a] * KY / K2;
+                acc[a] += amp * (re * cs - im * sn);
+            }
+        }
+        for (int a = 0; a < 3; ++a) s[i * 3 + a] = acc[a];
+    }
     return OR_OK;
 }
 
@@ -640,7 +777,9 @@ static int face_flux(const or_cfg *c, const or_tab *T, const or_geo *g, const do
 /* number of face positions along ax for a given transverse cell row */
 static int face_positions(const or_cfg *c, const or_geo *g, int ax) { return c->bc[ax] == 0 ? g->N[ax] : g->N[ax] + 1; }
 
-int or_rhs(const or_cfg *c, const double *w, const double *wig, double *rhs)
+/* right-hand side; with fst (forcing on) the driving source of Sec. 6 is added: rho s to the
+ * momentum and rho s.v = s.(rho v) to the energy, Gauss-integrated like every volume term */
+int or_rhs_forced(const or_cfg *c, const double *w, const double *wig, const double *fst, double *rhs)
 {
     if (check_cfg(c)) return OR_EINVAL;
     or_geo g;
@@ -699,6 +838,21 @@ int or_rhs(const or_cfg *c, const double *w, const double *wig, double *rhs)
                 double adot = c->f_v * fmax(0.0, -div) + (wig ? wig[K] : 0.0) -
                               u[g.IA] * g.P * P.cs / (c->f_tau * g.hmin);
                 for (int l = 0; l < M; ++l) W(rhs, &g, g.IA, K, l) += two_d * T.G[j] * ph[l] * adot;
+            }
+            if (c->forcing_on && fst) {
+                int ci[3], jj[3];
+                cell_coords(&g, K, ci);
+                unflat(j, T.Q, d, jj);
+                double xp[3], sv[3];
+                for (int a = 0; a < d; ++a) xp[a] = c->lo[a] + (ci[a] + 0.5 + 0.5 * T.xg[jj[a]]) * g.h[a];
+                or_forcing_eval(c, fst, 1, xp, sv);
+                double src[OR_MAXF] = {0.0};
+                for (int a = 0; a < d; ++a) {
+                    src[1 + a] = u[0] * sv[a];
+                    src[d + 1] += sv[a] * u[1 + a];
+                }
+                for (int f = 1; f < d + 2; ++f)
+                    for (int l = 0; l < M; ++l) W(rhs, &g, f, K, l) += two_d * T.G[j] * ph[l] * src[f];
             }
         }
     }
@@ -966,12 +1120,22 @@ int or_rk_table(int s, double *alpha, double *beta)
     return OR_OK;
 }
 
+int or_rhs(const or_cfg *c, const double *w, const double *wig, double *rhs)
+{
+    if (c->forcing_on) return OR_EINVAL; /* the forcing state is an argument of or_rhs_forced */
+    return or_rhs_forced(c, w, wig, NULL, rhs);
+}
+
 /* one SSP-RK step of size dt (dt <= 0: CFL time step of the current state).
  * w is advanced in place; S_prev/wig are the per-cell sensor scalars;
- * scal = {dt_prev, step, t} is updated; dt_used receives the step size. */
-int or_step(const or_cfg *c, double *w, double *S_prev, double *wig, double *scal, double dt, double *dt_used)
+ * scal = {dt_prev, step, t} is updated; dt_used receives the step size.
+ * With forcing on, fst is the forcing state: the OU updates due at the step's start time are
+ * applied first, and that driving field acts during every stage of the step. */
+int or_step_forced(const or_cfg *c, double *w, double *S_prev, double *wig, double *scal, double *fst, double dt,
+                   double *dt_used)
 {
     if (check_cfg(c)) return OR_EINVAL;
+    if (c->forcing_on && !fst) return OR_EINVAL;
     or_geo g;
     geo_init(&g, c);
     int s = c->rk_stages > 0 ? c->rk_stages : or_rk_stages(c->n);
@@ -984,6 +1148,7 @@ int or_step(const or_cfg *c, double *w, double *S_prev, double *wig, double *sca
      * initial data (a projected discontinuity can be negative at points) */
     if (c->positivity_on) status |= or_positivity(c, w);
     if (c->av_on) status |= or_wiggle(c, w, S_prev, wig, scal[0], (long)scal[1]);
+    if (c->forcing_on) status |= or_forcing_update(c, fst, scal[2]);
     if (!(dt > 0.0)) status |= or_max_dt(c, w, &dt);
     if (status & OR_EINVAL) return status;
     double *U[6], *L[6];
@@ -993,7 +1158,7 @@ int or_step(const or_cfg *c, double *w, double *S_prev, double *wig, double *sca
     }
     memcpy(U[0], w, sizeof(double) * nw);
     for (int i = 1; i <= s; ++i) {
-        status |= or_rhs(c, U[i - 1], c->av_on ? wig : NULL, L[i - 1]);
+        status |= or_rhs_forced(c, U[i - 1], c->av_on ? wig : NULL, c->forcing_on ? fst : NULL, L[i - 1]);
         for (size_t q = 0; q < nw; ++q) {
             double acc = 0.0;
             for (int k = 0; k < i; ++k) {
@@ -1014,6 +1179,11 @@ int or_step(const or_cfg *c, double *w, double *S_prev, double *wig, double *sca
     scal[2] += dt;
     if (dt_used) *dt_used = dt;
     return status;
+}
+
+int or_step(const or_cfg *c, double *w, double *S_prev, double *wig, double *scal, double dt, double *dt_used)
+{
+    return or_step_forced(c, w, S_prev, wig, scal, NULL, dt, dt_used);
 }
 
 /* basis values phi_l at arbitrary reference points xi[npts][d] -> out[npts][M] */
