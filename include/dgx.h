@@ -78,7 +78,19 @@ typedef struct dg_grid {
  *  positivity_on: 1 applies the positivity limiter of Sec. 4.2 after every
  *             stage (rho_bottom = 1e-6 mean rho, p_bottom = 1e-6 p(mean state),
  *             at most 60 pressure halvings; a cell that still fails, or whose
- *             mean state is non-physical, sets the status word). */
+ *             mean state is non-physical, sets the status word).
+ *  forcing_on: 1 adds the turbulence driving of Sec. 6: an acceleration s(x)
+ *             of Fourier modes 2pi/L <= |k| <= 2 (2pi/L) (one of each +-k
+ *             pair: 6 in 2-D, 16 in 3-D), amplitude force_amp |k|^(-5/3) with
+ *             |k| in units of 2pi/L, complex vector coefficients that follow
+ *             Ornstein-Uhlenbeck processes of correlation time force_ts > 0,
+ *             advanced exactly at times j * force_dt (force_dt > 0) from
+ *             counter-based SplitMix64 + Box-Muller draws of force_seed, and
+ *             projected onto the plane normal to k (solenoidal).  The source
+ *             rho s enters the momentum and s.(rho v) the energy, integrated
+ *             with the volume Gauss rule.  Each step applies the updates due at
+ *             its start time and keeps that field for all of its stages.
+ *             Defaults: off, force_amp 0, force_ts 1, force_dt 0.01, seed 0. */
 typedef struct dg_params {
     int precision;
     int rk_stages;
@@ -86,6 +98,9 @@ typedef struct dg_params {
     int av_on;
     double av_scale, f_v, f_tau, f_w, s_onset;
     int positivity_on;
+    int forcing_on;
+    double force_amp, force_ts, force_dt;
+    unsigned long long force_seed;
 } dg_params;
 
 /* Fill p with the defaults listed above (DG_FP64, automatic RK, AV off). */
@@ -120,7 +135,8 @@ int dg_get_state_device(dg_t *h, double *dev_w);
 /* Right-hand side L(w) = dw/dt of Eq. weight_evolution (volume integral,
  * HLLC surface flux, recovered-gradient viscous and artificial-viscosity
  * fluxes of Sec. 3, alpha source of Eq. timedependentviscosity) of the
- * current state, with the per-cell wiggle term as stored (dg_set_aux).
+ * current state, with the per-cell wiggle term as stored (dg_set_aux) and,
+ * with forcing on, the driving field of the current forcing state (no update).
  * No time advance.  Output in the state layout, float64. */
 int dg_rhs(dg_t *h, double *host_out);
 int dg_rhs_device(dg_t *h, double *dev_out);
@@ -158,6 +174,17 @@ int dg_conserved_sums(dg_t *h, double *out);
  * count, time}.  Any pointer may be NULL to skip it. */
 int dg_get_aux(dg_t *h, double *S_prev, double *wig, double *scal);
 int dg_set_aux(dg_t *h, const double *S_prev, const double *wig, const double *scal);
+
+/* Driving (forcing) state, DG_FORCING_STATE doubles: [0] index of the last OU update
+ * applied (-1: none yet; the first step draws the stationary state), then for each of the
+ * 16 mode slots (6 used in 2-D, in the order: kz outer, ky, kx inner over the integer vectors
+ * with 1 <= |k|^2 <= 4 whose first non-zero component is positive) the real and imaginary
+ * parts of the OU vector, x y z each (components beyond d are zero).  For checkpoints and
+ * for restarting a run bit for bit; a state set with dg_set_forcing takes effect at the next
+ * dg_step or dg_rhs.  DG_EINVAL when forcing is off. */
+#define DG_FORCING_STATE 97
+int dg_get_forcing(dg_t *h, double *host_state);
+int dg_set_forcing(dg_t *h, const double *host_state);
 
 /* The CFL time step of Eq. timestep, like dg_max_dt, for callers that cannot
  * let a library allocate device memory: code that hands all device memory to

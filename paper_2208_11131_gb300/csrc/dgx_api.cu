@@ -162,6 +162,7 @@ __global__ void batch_dt_kernel(const StageArgs *d, int nsims, int P, double fix
 }
 
 constexpr int kSumBlocks = 256;
+constexpr int kMaxEvents = 12;
 constexpr int kMaxStageGrid = 16384;  // persistent stage grid: SMs x resident CTAs (upper bound)
 
 }  // namespace
@@ -200,7 +201,16 @@ struct dg_handle {
     cudaGraphExec_t graph = nullptr;
     double graph_dt = 0.0;
 
-    cudaEvent_t ev[8] = {nullptr};  // per-launch timing events of dg_step_timed
+    // turbulence driving (Sec. 6)
+    ForcingModes fm;
+    double *fstate = nullptr;  // [kForceState] OU state
+    double *smodes = nullptr;  // [kForceModes][6] projected, scaled amplitudes
+    void *force = nullptr;     // Real [d][cell][node] driving acceleration
+    void *ftab = nullptr;      // Real per-axis phase tables
+    long long ftab_off[3] = {0, 0, 0};
+    int forced_last = 0;  // the last enqueued step ran the driving kernels
+
+    cudaEvent_t ev[kMaxEvents] = {nullptr};  // per-launch timing events of dg_step_timed
 
     std::string err;
 };
@@ -252,6 +262,58 @@ void free_buffers(dg_t *h)
     cudaFree(h->status);
     h->Sprev = h->wig = h->dtp = h->partial = h->sums = h->rhs_tmp = nullptr;
     h->status = nullptr;
+    cudaFree(h->fstate);
+    cudaFree(h->smodes);
+    cudaFree(h->force);
+    cudaFree(h->ftab);
+    h->fstate = h->smodes = nullptr;
+    h->force = h->ftab = nullptr;
+}
+
+// driving buffers (allocated while forcing is on; the OU state starts with no update applied)
+int alloc_forcing(dg_t *h)
+{
+    double L[3] = {1.0, 1.0, 1.0};
+    for (int a = 0; a < h->dim; ++a) L[a] = h->grid.hi[a] - h->grid.lo[a];
+    forcing_modes(h->dim, L, h->p.force_amp, &h->fm);
+    if (h->force) return DG_OK;
+    const size_t rs = real_size(h);
+    long long ntab = 0;
+    for (int a = 0; a < h->dim; ++a) ntab += (long long)h->grid.n[a] * h->Q * 10;
+    std::vector<double> tab((size_t)ntab);
+    forcing_phase_tables(h->dim, h->grid.n, L, h->degree, tab.data(), h->ftab_off);
+    std::vector<float> tabf(fp32(h) ? (size_t)ntab : 0);
+    for (size_t i = 0; i < tabf.size(); ++i) tabf[i] = (float)tab[i];
+    const size_t nforce = (size_t)h->dim * h->ncell * h->M;
+    if (cudaMalloc(&h->force, nforce * rs) != cudaSuccess || cudaMalloc(&h->ftab, (size_t)ntab * rs) != cudaSuccess ||
+        cudaMalloc((void **)&h->fstate, kForceState * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void **)&h->smodes, 6 * kForceModes * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(h->force);
+        cudaFree(h->ftab);
+        cudaFree(h->fstate);
+        cudaFree(h->smodes);
+        h->force = h->ftab = nullptr;
+        h->fstate = h->smodes = nullptr;
+        return fail(h, DG_ENOMEM, "driving buffers");
+    }
+    std::vector<double> f0(kForceState, 0.0);
+    f0[0] = -1.0;
+    CK(h, cudaMemcpy(h->ftab, fp32(h) ? (const void *)tabf.data() : (const void *)tab.data(), (size_t)ntab * rs,
+                     cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->fstate, f0.data(), kForceState * sizeof(double), cudaMemcpyHostToDevice));
+    CK(h, cudaMemset(h->smodes, 0, 6 * kForceModes * sizeof(double)));
+    CK(h, cudaMemset(h->force, 0, nforce * rs));
+    return DG_OK;
+}
+
+// driving acceleration at the volume nodes from the current amplitudes
+cudaError_t launch_forcing_eval_any(const dg_t *h)
+{
+    return fp32(h) ? launch_forcing_eval_f32(h->dim, h->degree, h->grid.n, h->ncell, (const float *)h->ftab,
+                                             h->ftab_off, h->smodes, (float *)h->force, h->stream)
+                   : launch_forcing_eval_f64(h->dim, h->degree, h->grid.n, h->ncell, (const double *)h->ftab,
+                                             h->ftab_off, h->smodes, (double *)h->force, h->stream);
 }
 
 int prepare_kernels(dg_t *h);
@@ -313,6 +375,10 @@ int alloc_buffers(dg_t *h)
     CK(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     h->cur = 0;
+    if (h->p.forcing_on) {
+        st = alloc_forcing(h);
+        if (st) return st;
+    }
     return prepare_kernels(h);
 }
 
@@ -339,6 +405,7 @@ void base_stage_args(const dg_t *h, StageArgs &a)
     a.wig = h->wig;
     a.dtp = h->dtp;
     a.status = h->status;
+    a.force = h->p.forcing_on ? h->force : nullptr;
 }
 
 cudaError_t launch_stage_any(const dg_t *h, const StageArgs &a_in, int *grid = nullptr)
@@ -464,6 +531,13 @@ int enqueue_step(dg_t *h, double dt, cudaEvent_t *ev = nullptr)
     const bool fused = S.stages >= 2 && !h->p.positivity_on;
     int ne = 0;
     if (ev) CK(h, cudaEventRecord(ev[ne++], h->stream));
+    if (h->p.forcing_on) {
+        // driving updates due at the step's start time (device-resident t), then its field
+        CK(h, launch_forcing_update(h->fm, h->dim, h->p.force_dt, h->p.force_ts, h->p.force_seed, 1, h->fstate,
+                                    h->dtp + 2, h->smodes, h->status, h->stream));
+        CK(h, launch_forcing_eval_any(h));
+        if (ev) CK(h, cudaEventRecord(ev[ne++], h->stream));
+    }
     if (!fused) {
         if (h->p.positivity_on) {
             // the state entering the step is limited too (only initial data can need it)
@@ -514,6 +588,7 @@ int enqueue_step(dg_t *h, double dt, cudaEvent_t *ev = nullptr)
         }
     }
     h->fused_last = fused ? 1 : 0;
+    h->forced_last = h->p.forcing_on ? 1 : 0;
     h->nev = ne;
     h->cur = nx;
     return DG_OK;
@@ -529,6 +604,9 @@ int check_status(dg_t *h)
         CK(h, cudaStreamSynchronize(h->stream));
         if (st & DG_STATUS_NONPHYS)
             return fail(h, DG_ENONPHYS, "non-physical state (rho <= 0 or p <= 0) at a quadrature point");
+        if (st & DG_STATUS_FORCING)
+            return fail(h, DG_EINVAL, "more than %lld driving updates due in one step (force_dt too small)",
+                        kForceMaxUpdates);
         return fail(h, DG_ENONPHYS, "non-finite or non-positive time step");
     }
     return DG_OK;
@@ -573,6 +651,11 @@ int dg_default_params(dg_params *p)
     p->f_w = 0.2;
     p->s_onset = 1e-4;
     p->positivity_on = 0;
+    p->forcing_on = 0;
+    p->force_amp = 0.0;
+    p->force_ts = 1.0;
+    p->force_dt = 0.01;
+    p->force_seed = 0;
     return DG_OK;
 }
 
@@ -636,7 +719,7 @@ void dg_destroy(dg_t *h)
     cudaStreamSynchronize(h->stream);
     free_buffers(h);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < kMaxEvents; ++i)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);
     delete h;
 }
@@ -649,6 +732,9 @@ int dg_set_params(dg_t *h, const dg_params *p)
         (p->av_on != 0 && p->av_on != 1) || !(p->f_tau > 0.0) || p->av_scale < 0.0)
         return fail(h, DG_EINVAL, "invalid dg_params");
     if (p->positivity_on != 0 && p->positivity_on != 1) return fail(h, DG_EINVAL, "positivity_on must be 0 or 1");
+    if ((p->forcing_on != 0 && p->forcing_on != 1) ||
+        (p->forcing_on && (!(p->force_ts > 0.0) || !(p->force_dt > 0.0) || !(p->force_amp >= 0.0))))
+        return fail(h, DG_EINVAL, "forcing needs force_ts > 0, force_dt > 0, force_amp >= 0");
     const bool realloc = p->precision != h->p.precision || p->av_on != h->p.av_on;
     h->p = *p;
     if (h->graph) {
@@ -656,6 +742,7 @@ int dg_set_params(dg_t *h, const dg_params *p)
         h->graph = nullptr;
     }
     if (realloc) return alloc_buffers(h);
+    if (h->p.forcing_on) return alloc_forcing(h);
     return DG_OK;
 }
 
@@ -722,6 +809,12 @@ int dg_rhs_device(dg_t *h, double *dev_out)
     a.din = nullptr;
     a.mode = 0;
     a.rhs_out = dev_out;
+    if (h->p.forcing_on) {
+        // the field of the current driving state, without advancing it
+        CK(h, launch_forcing_update(h->fm, h->dim, h->p.force_dt, h->p.force_ts, h->p.force_seed, 0, h->fstate,
+                                    h->dtp + 2, h->smodes, h->status, h->stream));
+        CK(h, launch_forcing_eval_any(h));
+    }
     CK(h, launch_stage_any(h, a));
     return DG_OK;
 }
@@ -802,21 +895,25 @@ int dg_step_timed(dg_t *h, double dt, float *ms, int nms)
     const int ns = stage_count(h);
     const int nl = 2 + ns;
     if (nms < nl) return fail(h, DG_EINVAL, "dg_step_timed needs room for %d launch times", nl);
-    for (int i = 0; i <= nl; ++i)
+    for (int i = 0; i < kMaxEvents; ++i)
         if (!h->ev[i]) CK(h, cudaEventCreate(&h->ev[i]));
     int st = enqueue_step(h, dt, h->ev);
     if (st) return st;
     CK(h, cudaEventSynchronize(h->ev[h->nev - 1]));
-    float d[8];
+    float d[kMaxEvents];
     for (int i = 0; i + 1 < h->nev; ++i) CK(h, cudaEventElapsedTime(&d[i], h->ev[i], h->ev[i + 1]));
+    // the driving kernels (if any) run first; their time is counted with the step prologue
+    const int o = h->forced_last ? 1 : 0;
+    const float fms = h->forced_last ? d[0] : 0.0f;
     if (h->fused_last) {
         // launch order: stage 1 (with the prologue work), dt reduction, stages 2..s
-        ms[0] = 0.0f;
-        ms[2] = d[0];
-        ms[1] = d[1];
-        for (int i = 1; i < ns; ++i) ms[2 + i] = d[1 + i];
+        ms[0] = fms;
+        ms[2] = d[o];
+        ms[1] = d[o + 1];
+        for (int i = 1; i < ns; ++i) ms[2 + i] = d[o + 1 + i];
     } else {
-        for (int i = 0; i < nl; ++i) ms[i] = d[i];
+        for (int i = 0; i < nl; ++i) ms[i] = d[o + i];
+        ms[0] += fms;
     }
     return DG_OK;
 }
@@ -870,6 +967,23 @@ int dg_set_aux(dg_t *h, const double *S_prev, const double *wig, const double *s
         CK(h, cudaMemcpyAsync(h->Sprev, S_prev, h->ncell * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     if (wig) CK(h, cudaMemcpyAsync(h->wig, wig, h->ncell * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     if (scal) CK(h, cudaMemcpyAsync(h->dtp, scal, 3 * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return DG_OK;
+}
+
+int dg_get_forcing(dg_t *h, double *host_state)
+{
+    if (!h || !host_state) return DG_EINVAL;
+    if (!h->p.forcing_on || !h->fstate) return fail(h, DG_EINVAL, "forcing is off");
+    CK(h, cudaMemcpyAsync(host_state, h->fstate, kForceState * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return check_status(h);
+}
+
+int dg_set_forcing(dg_t *h, const double *host_state)
+{
+    if (!h || !host_state) return DG_EINVAL;
+    if (!h->p.forcing_on || !h->fstate) return fail(h, DG_EINVAL, "forcing is off");
+    CK(h, cudaMemcpyAsync(h->fstate, host_state, kForceState * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     return DG_OK;
 }
@@ -976,7 +1090,7 @@ int dg_batch_create(dg_t *const *sims, int count, dg_batch_t **out)
     for (int k = 0; k < count; ++k) {
         const dg_t *h = sims[k];
         if (!h) return DG_EINVAL;
-        if (h->p.positivity_on || stage_count(h) < 2) return DG_EUNSUPPORTED;
+        if (h->p.positivity_on || h->p.forcing_on || stage_count(h) < 2) return DG_EUNSUPPORTED;
         if (h->cur != sims[0]->cur || h->device != sims[0]->device || h->stream != sims[0]->stream)
             return DG_EINVAL;
     }

@@ -11,6 +11,7 @@ constexpr int kMaxDegree = 5;
 // bits of the device status word
 constexpr int DG_STATUS_NONPHYS = 1;  // rho <= 0, p <= 0 or non-finite value at a quadrature point
 constexpr int DG_STATUS_BADDT = 2;    // non-finite or non-positive CFL time step
+constexpr int DG_STATUS_FORCING = 4;  // more driving updates due in one step than the kernel applies
 constexpr int kMaxQ = kMaxDegree + 1;
 
 // Per-degree operator tables, host-generated in long double (dgx_tables.cu):
@@ -69,6 +70,7 @@ struct StageArgs {
     const void *ubase;  // Real*: FP32 high copy of u^n (bulk) or u^n itself (FP64)
     const void *din;    // Real*
     const double *wig;  // per cell wiggle source
+    const void *force;  // Real* driving acceleration at the volume nodes [d][cell][node], or null
     const double *dtp;  // device scalars {dt, step, t}
 
     // epilogue
@@ -196,6 +198,34 @@ cudaError_t launch_stage_batch_3d_f64(int degree, int av, int ns, const StageArg
                                       int nsims, int total, const Tables<double> &t, cudaStream_t s);
 cudaError_t launch_stage_batch_3d_f32(int degree, int av, int ns, const StageArgs *descs, const int *tile_off,
                                       int nsims, int total, const Tables<float> &t, cudaStream_t s);
+// ---- turbulence driving (Sec. 6), dgx_forcing.cu
+constexpr int kForceModes = 16;                  // mode stride of the forcing state (3-D count)
+constexpr int kForceState = 1 + 6 * kForceModes;  // last update index + (X_m, Y_m) per mode
+constexpr long long kForceMaxUpdates = 100000;    // per step; more sets DG_STATUS_FORCING
+
+// per-mode constants of the driving: physical wave vector K = 2 pi k / L and amplitude A |k|^(-5/3)
+struct ForcingModes {
+    int nm;
+    double K[kForceModes][3];
+    double amp[kForceModes];
+};
+// fills the modes of a dim-dimensional box of edge lengths L
+void forcing_modes(int dim, const double *L, double amp, ForcingModes *fm);
+// host-built per-axis tables exp(i 2 pi k x / L) at every (cell, Gauss node) along each axis,
+// k = -2..2: [(cell * (n+1) + i) * 5 + k + 2] (cos, sin); returns the offsets of the axes
+void forcing_phase_tables(int dim, const int *N, const double *L, int degree, double *out, long long *off);
+void gauss_nodes(int q, double *x);
+// advance = 1: apply the driving updates due at time *t to fstate; then (either way) write the
+// projected, scaled complex amplitudes (Re s_m, Im s_m) of fstate to smodes [kForceModes][6]
+cudaError_t launch_forcing_update(const ForcingModes &fm, int dim, double force_dt, double force_ts,
+                                  unsigned long long seed, int advance, double *fstate, const double *t,
+                                  double *smodes, int *status, cudaStream_t s);
+// driving acceleration at every volume node: out [d][cell][node]
+cudaError_t launch_forcing_eval_f64(int dim, int degree, const int *N, long long ncell, const double *tab,
+                                    const long long *off, const double *smodes, double *out, cudaStream_t s);
+cudaError_t launch_forcing_eval_f32(int dim, int degree, const int *N, long long ncell, const float *tab,
+                                    const long long *off, const double *smodes, float *out, cudaStream_t s);
+
 void tiles_2d_f64(int degree, int *stage, int *pro);
 void tiles_2d_f32(int degree, int *stage, int *pro);
 void tiles_3d_f64(int degree, int *stage, int *pro);

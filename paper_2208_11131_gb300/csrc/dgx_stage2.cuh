@@ -400,6 +400,21 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
 #pragma unroll
                     for (int f = 0; f < NC; ++f) sF[((a * NC + f) * TC + c) * NP + j] = w * F[f];
                 }
+                if (A.force) {
+                    // driving source of Sec. 6 at this node, Gauss-weighted like the alpha source:
+                    // rho s into the momentum, s.(rho v) into the energy; the conserved part of sR
+                    // is free until the residual phase, which adds it
+                    const Real *fs = static_cast<const Real *>(A.force);
+                    const Real wgt = src_w * Gv;
+                    Real se = Real(0);
+#pragma unroll
+                    for (int a = 0; a < DIM; ++a) {
+                        const Real sa = fs[((size_t)a * A.ncell + g) * NP + j];
+                        sR[((1 + a) * TC + c) * NP + j] = wgt * u[0] * sa;
+                        se = fma(sa, u[1 + a], se);
+                    }
+                    sR[((DIM + 1) * TC + c) * NP + j] = wgt * se;
+                }
                 if (AV) {
                     Real div = Real(0);
 #pragma unroll
@@ -587,6 +602,7 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                 r = fma(tLm[i], sFh[(f * NFACE + fl) * NPF + k], r);
                 r = fma(-tLp[i], sFh[(f * NFACE + fl + 1) * NPF + k], r);
             }
+            if (A.force && f > 0) r += sR[idx];
             sR[idx] = r;
         }
         __syncthreads();

@@ -170,4 +170,11 @@ void make_tables(int n, Tables<double> *td, Tables<float> *tf)
     *tf = F;
 }
 
+void gauss_nodes(int q, double *x)
+{
+    LD xl[kMaxQ + 2], wl[kMaxQ + 2];
+    gauss_rule(q, xl, wl);
+    for (int i = 0; i < q; ++i) x[i] = (double)xl[i];
+}
+
 }  // namespace dgx

@@ -29,6 +29,7 @@ EXPORTS = (
     "dg_rhs", "dg_rhs_device", "dg_step", "dg_steps", "dg_step_timed", "dg_sync", "dg_max_dt", "dg_conserved_sums",
     "dg_get_aux", "dg_set_aux", "dg_last_error", "dg_status_string", "dg_max_dt_noalloc",
     "dg_batch_create", "dg_batch_step", "dg_batch_sync", "dg_batch_last_error", "dg_batch_destroy",
+    "dg_get_forcing", "dg_set_forcing",
 )
 
 
@@ -41,7 +42,10 @@ class dg_params(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("rk_stages", ctypes.c_int), ("cfl", ctypes.c_double),
                 ("av_on", ctypes.c_int), ("av_scale", ctypes.c_double), ("f_v", ctypes.c_double),
                 ("f_tau", ctypes.c_double), ("f_w", ctypes.c_double), ("s_onset", ctypes.c_double),
-                ("positivity_on", ctypes.c_int)]
+                ("positivity_on", ctypes.c_int), ("forcing_on", ctypes.c_int), ("force_amp", ctypes.c_double),
+                ("force_ts", ctypes.c_double), ("force_dt", ctypes.c_double), ("force_seed", ctypes.c_ulonglong)]
+
+FORCING_STATE = 97  # DG_FORCING_STATE
 
 
 class DGError(RuntimeError):
@@ -86,6 +90,7 @@ def lib(path: str = LIB_PATH):
         "dg_batch_last_error": (ctypes.c_char_p, [H]), "dg_batch_destroy": (None, [H]),
         "dg_max_dt_noalloc": (I, [ctypes.POINTER(dg_grid), I, ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_void_p]),
+        "dg_get_forcing": (I, [H, P]), "dg_set_forcing": (I, [H, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -215,6 +220,18 @@ def dg_set_aux(h, S_prev=None, wig=None, scal=None):
     _check(h, lib().dg_set_aux(h, _dp(S_prev), _dp(wig), _dp(scal)))
 
 
+def dg_get_forcing(h) -> np.ndarray:
+    out = np.zeros(FORCING_STATE)
+    _check(h, lib().dg_get_forcing(h, _dp(out)))
+    return out
+
+
+def dg_set_forcing(h, state):
+    state = np.ascontiguousarray(state, dtype=np.float64)
+    assert state.shape == (FORCING_STATE,)
+    _check(h, lib().dg_set_forcing(h, _dp(state)))
+
+
 def dg_max_dt_noalloc(grid: dg_grid, degree: int, gamma: float, cfl: float, dev_state_ptr: int, dev_dt_ptr: int,
                       stream_ptr: int = 0):
     """CFL step into a caller-owned device double; allocates nothing (see include/dgx.h)."""
@@ -275,6 +292,10 @@ class Simulation:
         p.cfl = wl.cfl if cfl is None else cfl
         p.av_on = int(wl.av_on)
         p.positivity_on = int(getattr(wl, "positivity_on", 0))
+        if getattr(wl, "forcing_on", 0):
+            p.forcing_on = 1
+            p.force_amp, p.force_ts, p.force_dt = wl.force_amp, wl.force_ts, wl.force_dt
+            p.force_seed = int(wl.force_seed) & 0xFFFFFFFFFFFFFFFF
         dg_set_params(self.h, p)
         self.nf, self.M, self.ncell = dg_sizes(self.h)
         self.nc = wl.dim + 2
@@ -326,6 +347,12 @@ class Simulation:
 
     def conserved_sums(self) -> np.ndarray:
         return dg_conserved_sums(self.h, self.nc)
+
+    def get_forcing(self) -> np.ndarray:
+        return dg_get_forcing(self.h)
+
+    def set_forcing(self, state):
+        dg_set_forcing(self.h, state)
 
     def get_aux(self):
         return dg_get_aux(self.h, self.ncell)

@@ -41,6 +41,13 @@ class Workload:
     positivity_on: int = 0
     cfl: float = 0.5
     steps: int = 1
+    # turbulence driving (Sec. 6): amplitude of the |k| = 1 modes, OU correlation time, update
+    # interval, generator seed
+    forcing_on: int = 0
+    force_amp: float = 0.0
+    force_ts: float = 1.0
+    force_dt: float = 0.01
+    force_seed: int = 0
 
     @property
     def ncell(self) -> int:
@@ -95,9 +102,13 @@ def c3_sod_blast(N: int = 64, n: int = 3) -> Workload:
 
 
 def c4_turbulence_box(N: int = 128, n: int = 3) -> Workload:
-    """3-D periodic subsonic turbulence box, gamma=1.001, nu=kappa=1e-4, AV on."""
+    """3-D periodic subsonic turbulence box, gamma=1.001, nu=kappa=1e-4, AV on, driven (Sec. 6):
+    modes 1 <= |k| <= 2, amplitude 0.03 |k|^(-5/3) (rms acceleration about 0.1, which brings the
+    gas started at rest with c_s = 1 to Mach ~0.3 within a few time units), OU correlation time 1,
+    update interval 0.01."""
     return Workload("turbulence_box_3d", 3, n, (N, N, N), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), gamma=1.001,
-                    nu=1e-4, kappa=1e-4, av_on=1, cfl=0.5, steps=100)
+                    nu=1e-4, kappa=1e-4, av_on=1, cfl=0.5, steps=100, forcing_on=1, force_amp=0.03,
+                    force_ts=1.0, force_dt=0.01, force_seed=BASE_SEED + 4)
 
 
 # ------------------------------------------------------------------ projection (numpy Gauss rule)
@@ -197,6 +208,15 @@ def sod_blast_ic(wl: Workload, seed: int = BASE_SEED):
         zero = np.zeros_like(rho)
         return _cons(wl.gamma, rho, [zero] * wl.dim, p, zero if wl.av_on else None)
     return f
+
+
+def rest_state(wl: Workload) -> np.ndarray:
+    """modes of gas at rest with uniform density 1 and pressure 1/gamma (sound speed 1): the
+    starting state of the driven-turbulence runs of Sec. 6"""
+    w = np.zeros(wl.shape())
+    w[0, :, 0] = 1.0
+    w[wl.dim + 1, :, 0] = 1.0 / (wl.gamma * (wl.gamma - 1.0))
+    return w
 
 
 def sod_tube_ic(wl: Workload, axis: int = 0, x0: float = 0.5):
