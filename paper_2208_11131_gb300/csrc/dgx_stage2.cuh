@@ -45,10 +45,15 @@ struct Stage2Plan {
     static constexpr int NF = NC + (AV ? 1 : 0);
     static constexpr int TC = S::TC, NSLOT = S::NSLOT, NFACE = S::NFACE;
     static constexpr int TAB = (3 * Q * Q + 7 * Q + 1 + 3) / 4 * 4;
-    static constexpr int SZ_IN = PF ? NF * NSLOT * NP : 0;  // one prefetch array (u^n or delta), tile + halo
-    static constexpr int SZ_U = NF * NSLOT * NP;
-    static constexpr int SZ_F = DIM * NC * TC * NP;
-    static constexpr int SZ_R = NF * TC * NP;
+    // per-cell stride of the cell arrays in shared memory: one 16-byte unit more than a cell's
+    // values when those fill whole units, so that the strided (y, z) line accesses of the cells
+    // a warp touches spread over the banks; vector line accesses stay aligned
+    static constexpr int NPS = NP + ((NP * (int)sizeof(Real)) % 16 == 0 ? 16 / (int)sizeof(Real) : 0);
+    static constexpr int U16 = 16 / (int)sizeof(Real);  // values per 16 bytes; arrays are whole units
+    static constexpr int SZ_IN = PF ? (NF * NSLOT * NPS + U16 - 1) / U16 * U16 : 0;  // u^n or delta, tile + halo
+    static constexpr int SZ_U = (NF * NSLOT * NPS + U16 - 1) / U16 * U16;
+    static constexpr int SZ_F = (DIM * NC * TC * NPS + U16 - 1) / U16 * U16;
+    static constexpr int SZ_R = (NF * TC * NPS + U16 - 1) / U16 * U16;
     static constexpr int SZ_UT = NS ? NC * NFACE * NPF : 0;
     static constexpr int SZ_FH = NC * NFACE * NPF;
     static constexpr int OFF_IN0 = TAB;
@@ -64,7 +69,67 @@ struct Stage2Plan {
     // bytes of one cell's modes of one field; async copies use the widest legal chunk
     static constexpr int CELL_BYTES = NP * (int)sizeof(Real);
     static constexpr int CHUNK = CELL_BYTES % 16 == 0 ? 16 : (CELL_BYTES % 8 == 0 ? 8 : 4);
+    // widest access to one x-line of Q contiguous values (line starts are multiples of Q values
+    // from a cell start, cell starts multiples of NPS values from an array start)
+    static constexpr int LINE_BYTES = Q * (int)sizeof(Real);
+    static constexpr int VEC = LINE_BYTES % 16 == 0 ? 16 : (LINE_BYTES % 8 == 0 ? 8 : (int)sizeof(Real));
+    static_assert((NPS * (int)sizeof(Real)) % VEC == 0, "cell stride breaks line alignment");
+    static_assert((OFF_IN0 * (int)sizeof(Real)) % 16 == 0 && (OFF_IN1 * (int)sizeof(Real)) % 16 == 0 &&
+                      (OFF_U * (int)sizeof(Real)) % 16 == 0 && (OFF_R * (int)sizeof(Real)) % 16 == 0,
+                  "cell arrays must start on 16-byte boundaries");
 };
+
+// one x-line of Q contiguous values from / to shared or global memory with the widest aligned
+// accesses (VEC bytes; the caller guarantees VEC alignment of p)
+template <int Q, int VEC, typename T>
+__device__ __forceinline__ void ld_line(const T *p, T (&w)[Q])
+{
+    if constexpr (VEC == 16 && sizeof(T) == 4) {
+#pragma unroll
+        for (int m = 0; m < Q; m += 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(p + m);
+            w[m] = v.x;
+            w[m + 1] = v.y;
+            w[m + 2] = v.z;
+            w[m + 3] = v.w;
+        }
+    } else if constexpr (VEC >= 8 && sizeof(T) == 4) {
+#pragma unroll
+        for (int m = 0; m < Q; m += 2) {
+            const float2 v = *reinterpret_cast<const float2 *>(p + m);
+            w[m] = v.x;
+            w[m + 1] = v.y;
+        }
+    } else if constexpr (VEC == 16 && sizeof(T) == 8) {
+#pragma unroll
+        for (int m = 0; m < Q; m += 2) {
+            const double2 v = *reinterpret_cast<const double2 *>(p + m);
+            w[m] = v.x;
+            w[m + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < Q; ++m) w[m] = p[m];
+    }
+}
+
+template <int Q, int VEC, typename T>
+__device__ __forceinline__ void st_line(T *p, const T (&w)[Q])
+{
+    if constexpr (VEC == 16 && sizeof(T) == 4) {
+#pragma unroll
+        for (int m = 0; m < Q; m += 4) *reinterpret_cast<float4 *>(p + m) = make_float4(w[m], w[m + 1], w[m + 2], w[m + 3]);
+    } else if constexpr (VEC >= 8 && sizeof(T) == 4) {
+#pragma unroll
+        for (int m = 0; m < Q; m += 2) *reinterpret_cast<float2 *>(p + m) = make_float2(w[m], w[m + 1]);
+    } else if constexpr (VEC == 16 && sizeof(T) == 8) {
+#pragma unroll
+        for (int m = 0; m < Q; m += 2) *reinterpret_cast<double2 *>(p + m) = make_double2(w[m], w[m + 1]);
+    } else {
+#pragma unroll
+        for (int m = 0; m < Q; ++m) p[m] = w[m];
+    }
+}
 
 // Body shared by the single-simulation kernel (A0: its arguments) and the batched kernel (descs:
 // one argument set per simulation; tile_off: prefix sums of the simulations' tile counts, so the
@@ -76,7 +141,7 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
     using S = Shape<DIM, N, TX, TY, TZ>;
     using PL = Stage2Plan<DIM, N, Real, AV, NS, TX, TY, TZ, PF>;
     constexpr int Q = S::Q, NP = S::NP, NPF = S::NPF, NC = S::NC, TC = S::TC, NSLOT = S::NSLOT;
-    constexpr int NF = PL::NF, NFACE = S::NFACE;
+    constexpr int NF = PL::NF, NFACE = S::NFACE, NPS = PL::NPS, VEC = PL::VEC;
     constexpr bool GRAD = AV || NS;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -155,7 +220,7 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
             const int g = sG[slot];
             if (g < 0) continue;
             const size_t gbyte = (((size_t)f * T.ncell + g) * NP) * sizeof(Real) + (size_t)c * PL::CHUNK;
-            const size_t sbyte = ((size_t)(f * NSLOT + slot) * NP) * sizeof(Real) + (size_t)c * PL::CHUNK;
+            const size_t sbyte = ((size_t)(f * NSLOT + slot) * NPS) * sizeof(Real) + (size_t)c * PL::CHUNK;
             const char *gu = reinterpret_cast<const char *>(ub) + gbyte;
             char *su = reinterpret_cast<char *>(sIn0) + sbyte;
             if (PL::CHUNK == 16) cp_async_16(su, gu);
@@ -237,7 +302,7 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                 const int g = sG[fs % NSLOT];
                 if (g < 0) continue;
                 const size_t gi = ((size_t)(fs / NSLOT) * A.ncell + g) * NP + l;
-                sU[idx] = ub[gi] + (di ? dsc * di[gi] : Real(0));
+                sU[fs * NPS + l] = ub[gi] + (di ? dsc * di[gi] : Real(0));
             }
             __syncthreads();
         }
@@ -251,7 +316,7 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                     continue;
                 }
                 Real hi = Real(0), all = Real(0);
-                const Real *w0 = modal + c * NP;  // density field, slot c
+                const Real *w0 = modal + c * NPS;  // density field, slot c
 #pragma unroll
                 for (int l = 0; l < NP; ++l) {
                     const int l0 = l % Q, l1 = (l / Q) % Q, l2 = DIM == 3 ? l / (Q * Q) : 0;
@@ -287,20 +352,28 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                 const int fs = idx / (NP / Q);
                 const int r = idx % (NP / Q);
                 if (sG[fs % NSLOT] < 0) continue;
-                const int base = fs * NP + r * Q;
+                const int base = fs * NPS + r * Q;
                 Real w[Q];
+                if constexpr (PF) {
+                    ld_line<Q, VEC>(sIn0 + base, w);
+                    if (di) {
+                        Real dd[Q];
+                        ld_line<Q, VEC>(sIn1 + base, dd);
 #pragma unroll
-                for (int m = 0; m < Q; ++m) {
-                    if constexpr (PF) w[m] = sIn0[base + m] + (di ? dsc * sIn1[base + m] : Real(0));
-                    else w[m] = sU[base + m];
+                        for (int m = 0; m < Q; ++m) w[m] = fma(dsc, dd[m], w[m]);
+                    }
+                } else {
+                    ld_line<Q, VEC>(sU + base, w);
                 }
+                Real o[Q];
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
                     Real acc = Real(0);
 #pragma unroll
                     for (int m = 0; m < Q; ++m) acc = fma(Tg.B[i][m], w[m], acc);
-                    sU[base + i] = acc;
+                    o[i] = acc;
                 }
+                st_line<Q, VEC>(sU + base, o);
             }
         }
         __syncthreads();
@@ -322,7 +395,7 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                 if (sG[fs % NSLOT] < 0) continue;
                 // r enumerates the (Q^(d-1)) positions transverse to axis a
                 const int lo = r % Sa, hi = r / Sa;
-                const int base = fs * NP + lo + hi * Sa * Q;
+                const int base = fs * NPS + lo + hi * Sa * Q;
                 Real w[Q];
 #pragma unroll
                 for (int m = 0; m < Q; ++m) w[m] = sU[base + m * Sa];
@@ -346,7 +419,7 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                 if (g < 0) continue;
                 Real u[NC + 1];
 #pragma unroll
-                for (int f = 0; f < NF; ++f) u[f] = sU[(f * NSLOT + c) * NP + j];
+                for (int f = 0; f < NF; ++f) u[f] = sU[(f * NSLOT + c) * NPS + j];
                 Real gr[DIM][NC];
                 if (GRAD) {
 #pragma unroll
@@ -356,7 +429,7 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                         const int base = j - i * Sa;
 #pragma unroll
                         for (int f = 0; f < NC; ++f) {
-                            const Real *p = sU + (f * NSLOT + c) * NP + base;
+                            const Real *p = sU + (f * NSLOT + c) * NPS + base;
                             Real acc = Real(0);
 #pragma unroll
                             for (int m = 0; m < Q; ++m) acc = fma(tDn[i * Q + m], p[m * Sa], acc);
@@ -398,7 +471,7 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                         if (q != a) Gp *= tG[jj[q]];
                     const Real w = cax[a] * Gp;
 #pragma unroll
-                    for (int f = 0; f < NC; ++f) sF[((a * NC + f) * TC + c) * NP + j] = w * F[f];
+                    for (int f = 0; f < NC; ++f) sF[((a * NC + f) * TC + c) * NPS + j] = w * F[f];
                 }
                 if (A.force) {
                     // driving source of Sec. 6 at this node, Gauss-weighted like the alpha source:
@@ -410,17 +483,17 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
 #pragma unroll
                     for (int a = 0; a < DIM; ++a) {
                         const Real sa = fs[((size_t)a * A.ncell + g) * NP + j];
-                        sR[((1 + a) * TC + c) * NP + j] = wgt * u[0] * sa;
+                        sR[((1 + a) * TC + c) * NPS + j] = wgt * u[0] * sa;
                         se = fma(sa, u[1 + a], se);
                     }
-                    sR[((DIM + 1) * TC + c) * NP + j] = wgt * se;
+                    sR[((DIM + 1) * TC + c) * NPS + j] = wgt * se;
                 }
                 if (AV) {
                     Real div = Real(0);
 #pragma unroll
                     for (int a = 0; a < DIM; ++a) div += (gr[a][1 + a] - v[a] * gr[a][0]) / rho;
                     const Real adot = f_v * fmax(Real(0), -div) + sWig[c] - u[NC] * cs * inv_tau;
-                    sR[(NC * TC + c) * NP + j] = src_w * Gv * adot;
+                    sR[(NC * TC + c) * NPS + j] = src_w * Gv * adot;
                 }
             }
             if (NS) {
@@ -449,8 +522,8 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                         const int sr = pp < V[a] ? cr[0] + TX * (cr[1] + TY * cr[2]) : S::HOFF(a, 1) + t;
                         if (sG[sl] < 0 || sG[sr] < 0) continue;
                         const int base = S::knode(a, 0, k);
-                        const Real *pl = sU + (f * NSLOT + sl) * NP + base;
-                        const Real *pr = sU + (f * NSLOT + sr) * NP + base;
+                        const Real *pl = sU + (f * NSLOT + sl) * NPS + base;
+                        const Real *pr = sU + (f * NSLOT + sr) * NPS + base;
                         Real acc = Real(0);
 #pragma unroll
                         for (int m = 0; m < Q; ++m) acc = fma(Tg.Cm[m], pl[m * Sa], fma(Tg.Cp[m], pr[m * Sa], acc));
@@ -495,7 +568,7 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                 Real u[NC], v[3], rho, pr_, cs;
 #pragma unroll
                 for (int f = 0; f < NC; ++f) {
-                    const Real *q = sU + (f * NSLOT + si) * NP + base;
+                    const Real *q = sU + (f * NSLOT + si) * NPS + base;
                     Real acc = Real(0);
 #pragma unroll
                     for (int m = 0; m < Q; ++m) acc = fma(right_in ? Tg.Lm[m] : Tg.Lp[m], q[m * Sa], acc);
@@ -507,8 +580,8 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                 Real uL[NC + 1], uR[NC + 1];
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
-                    const Real *ql = sU + (f * NSLOT + sl) * NP + base;
-                    const Real *qr = sU + (f * NSLOT + sr) * NP + base;
+                    const Real *ql = sU + (f * NSLOT + sl) * NPS + base;
+                    const Real *qr = sU + (f * NSLOT + sr) * NPS + base;
                     Real al = Real(0), ar = Real(0);
 #pragma unroll
                     for (int m = 0; m < Q; ++m) {
@@ -525,8 +598,8 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                     const Real sc = inv_f * inv_h[a];
 #pragma unroll
                     for (int f = 0; f < NC; ++f) {
-                        const Real *ql = sU + (f * NSLOT + sl) * NP + base;
-                        const Real *qr = sU + (f * NSLOT + sr) * NP + base;
+                        const Real *ql = sU + (f * NSLOT + sl) * NPS + base;
+                        const Real *qr = sU + (f * NSLOT + sr) * NPS + base;
                         Real acc = Real(0);
 #pragma unroll
                         for (int m = 0; m < Q; ++m) acc = fma(Tg.Dm[m], ql[m * Sa], fma(Tg.Dp[m], qr[m * Sa], acc));
@@ -593,7 +666,7 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
             for (int a = 0; a < DIM; ++a) {
                 const int Sa = S::S(a);
                 const int i = (n / Sa) % Q;
-                const Real *Fp = sF + ((a * NC + f) * TC + c) * NP + (n - i * Sa);
+                const Real *Fp = sF + ((a * NC + f) * TC + c) * NPS + (n - i * Sa);
 #pragma unroll
                 for (int m = 0; m < Q; ++m) r = fma(tWd[i * Q + m], Fp[m * Sa], r);
                 const int tt = S::trans(a, cc[0], cc[1], cc[2]);
@@ -602,8 +675,9 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                 r = fma(tLm[i], sFh[(f * NFACE + fl) * NPF + k], r);
                 r = fma(-tLp[i], sFh[(f * NFACE + fl + 1) * NPF + k], r);
             }
-            if (A.force && f > 0) r += sR[idx];
-            sR[idx] = r;
+            const int ri = fc * NPS + n;
+            if (A.force && f > 0) r += sR[ri];
+            sR[ri] = r;
         }
         __syncthreads();
 
@@ -617,7 +691,7 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                 const int r = idx % (NP / Q);
                 if (sG[fc % TC] < 0) continue;
                 const int lo = r % Sa, hi = r / Sa;
-                const int base = fc * NP + lo + hi * Sa * Q;
+                const int base = fc * NPS + lo + hi * Sa * Q;
                 Real w[Q];
 #pragma unroll
                 for (int m = 0; m < Q; ++m) w[m] = sR[base + m * Sa];
@@ -641,10 +715,9 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                 const int c = fc % TC, f = fc / TC;
                 const int g = sG[c];
                 if (g < 0) continue;
-                const int base = fc * NP + r * Q;
+                const int base = fc * NPS + r * Q;
                 Real w[Q], L[Q];
-#pragma unroll
-                for (int m = 0; m < Q; ++m) w[m] = sR[base + m];
+                ld_line<Q, VEC>(sR + base, w);
 #pragma unroll
                 for (int l = 0; l < Q; ++l) {
                     Real acc = Real(0);
@@ -658,19 +731,45 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                     for (int l = 0; l < Q; ++l) A.rhs_out[gi + l] = (double)L[l];
                     continue;
                 }
+                // library-owned arrays: a line starts at a multiple of Q values, so the widest
+                // aligned access of the line's bytes is legal
+                constexpr int VD = (Q * 8) % 16 == 0 ? 16 : 8;
+                constexpr int VF = (Q * 4) % 16 == 0 ? 16 : ((Q * 4) % 8 == 0 ? 8 : 4);
+                Real din[Q], xv[Q], dnew[Q], zn[Q];
+                if (di) {
+                    ld_line<Q, VEC>(di + gi, din);
+#pragma unroll
+                    for (int l = 0; l < Q; ++l) din[l] = dsc * din[l];
+                } else {
+#pragma unroll
+                    for (int l = 0; l < Q; ++l) din[l] = Real(0);
+                }
+                if (readx) {
+                    ld_line<Q, VEC>(xb + gi, xv);
+                } else {
+#pragma unroll
+                    for (int l = 0; l < Q; ++l) xv[l] = Real(0);
+                }
 #pragma unroll
                 for (int l = 0; l < Q; ++l) {
                     const Real dtL = dt * L[l];
-                    const Real din = di ? dsc * di[gi + l] : Real(0);
-                    const Real x = readx ? xb[gi + l] : Real(0);
-                    const Real dnew = ca * din + cx * x + cb * dtL;
-                    if (A.write_z) xb[gi + l] = za * din + zx * x + zb * dtL;
-                    if (A.mode == 1) {
-                        dout[gi + l] = dnew;
-                    } else {
-                        const double un = A.uold[gi + l] + (double)dnew;
-                        A.unew[gi + l] = un;
-                        if (A.uhi_new) A.uhi_new[gi + l] = (float)un;
+                    dnew[l] = ca * din[l] + cx * xv[l] + cb * dtL;
+                    zn[l] = za * din[l] + zx * xv[l] + zb * dtL;
+                }
+                if (A.write_z) st_line<Q, VEC>(xb + gi, zn);
+                if (A.mode == 1) {
+                    st_line<Q, VEC>(dout + gi, dnew);
+                } else {
+                    double uo[Q], un[Q];
+                    ld_line<Q, VD>(A.uold + gi, uo);
+#pragma unroll
+                    for (int l = 0; l < Q; ++l) un[l] = uo[l] + (double)dnew[l];
+                    st_line<Q, VD>(A.unew + gi, un);
+                    if (A.uhi_new) {
+                        float uf[Q];
+#pragma unroll
+                        for (int l = 0; l < Q; ++l) uf[l] = (float)un[l];
+                        st_line<Q, VF>(A.uhi_new + gi, uf);
                     }
                 }
             }
