@@ -35,7 +35,7 @@ if ROOT not in sys.path:
 METRIC = "DOF-updates/s per GB300 (FP32-bulk vs FP64, same L1 error) + % HBM roofline"
 UNIT = "DOF-updates/s"
 FLUSH_BYTES = 256 << 20
-KERNEL_SRC = os.path.join(ROOT, "paper_2208_11131_gb300", "csrc", "dgx_kernels.cuh")
+KERNEL_SRCS = [os.path.join(ROOT, "paper_2208_11131_gb300", "csrc", f) for f in ("dgx_kernels.cuh", "dgx_stage2.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
 
 
@@ -131,6 +131,14 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def kernel_sha() -> str:
+    """sha256 over the stage kernel's sources (a traffic figure is only used for the kernel it was taken on)"""
+    h = hashlib.sha256()
+    for f in KERNEL_SRCS:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
+
+
 def traffic_for(key: str):
     """DRAM bytes per stage launch from a committed ncu summary, if the kernel source is unchanged."""
     try:
@@ -140,7 +148,7 @@ def traffic_for(key: str):
     ent = tab.get(key)
     if not ent:
         return None
-    sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+    sha = kernel_sha()
     return ent["bytes_per_launch"] if ent.get("kernel_sha256") == sha else None
 
 
