@@ -38,6 +38,8 @@ __device__ __forceinline__ void cp_async_4(void *smem, const void *gmem)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+constexpr int kStageThreads = 256;  // threads of every stage-kernel CTA
+
 template <int DIM, int N, typename Real, bool AV, bool NS, int TX, int TY, int TZ, bool PF>
 struct Stage2Plan {
     using S = Shape<DIM, N, TX, TY, TZ>;
@@ -155,7 +157,10 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
     int *sGb = sGa + NSLOT;
     __shared__ int s_status;
 
-    const int tid = threadIdx.x, nth = blockDim.x;
+    // every launch uses kStageThreads threads: loop strides are compile-time constants, so the
+    // per-thread loops unroll and their index arithmetic folds
+    const int tid = threadIdx.x;
+    constexpr int nth = kStageThreads;
     const int ntiles = BATCH ? tile_off[nsims] : A0->ntile[0] * A0->ntile[1] * A0->ntile[2];
     // simulation of a work-list tile (binary search in the prefix sums)
     auto sim_of = [&](int tile) -> int {
@@ -836,13 +841,13 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
 }
 
 template <int DIM, int N, typename Real, bool AV, bool NS, int TX, int TY, int TZ, bool PF>
-__global__ void __launch_bounds__(256) stage2_kernel(const StageArgs A, const Tables<Real> Tg)
+__global__ void __launch_bounds__(kStageThreads) stage2_kernel(const StageArgs A, const Tables<Real> Tg)
 {
     stage2_body<DIM, N, Real, AV, NS, TX, TY, TZ, PF, false>(&A, nullptr, nullptr, 1, Tg);
 }
 
 template <int DIM, int N, typename Real, bool AV, bool NS, int TX, int TY, int TZ, bool PF>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kStageThreads)
     stage2_batch_kernel(const StageArgs *descs, const int *tile_off, int nsims, const Tables<Real> Tg)
 {
     stage2_body<DIM, N, Real, AV, NS, TX, TY, TZ, PF, true>(nullptr, descs, tile_off, nsims, Tg);
@@ -866,7 +871,7 @@ cudaError_t run_stage2(const StageArgs &a, const Tables<Real> &t, cudaStream_t s
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k, 256, PL::BYTES);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k, kStageThreads, PL::BYTES);
         if (e != cudaSuccess) return e;
         if (blocks_per_sm < 1) blocks_per_sm = 1;
     }
@@ -874,7 +879,7 @@ cudaError_t run_stage2(const StageArgs &a, const Tables<Real> &t, cudaStream_t s
     if (tiles == 0) return cudaSuccess;
     const int grid = tiles < sms * blocks_per_sm ? tiles : sms * blocks_per_sm;
     if (grid_out) *grid_out = grid;
-    k<<<grid, 256, PL::BYTES, s>>>(a, t);
+    k<<<grid, kStageThreads, PL::BYTES, s>>>(a, t);
     return cudaGetLastError();
 }
 
@@ -896,13 +901,13 @@ cudaError_t run_stage2_batch(const StageArgs *descs, const int *tile_off, int ns
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k, 256, PL::BYTES);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k, kStageThreads, PL::BYTES);
         if (e != cudaSuccess) return e;
         if (blocks_per_sm < 1) blocks_per_sm = 1;
     }
     if (total_tiles == 0) return cudaSuccess;
     const int grid = total_tiles < sms * blocks_per_sm ? total_tiles : sms * blocks_per_sm;
-    k<<<grid, 256, PL::BYTES, s>>>(descs, tile_off, nsims, t);
+    k<<<grid, kStageThreads, PL::BYTES, s>>>(descs, tile_off, nsims, t);
     return cudaGetLastError();
 }
 
