@@ -522,8 +522,8 @@ void fill_stage_args(const dg_t *h, const Schedule &S, int i, int c, bool fused,
 //
 // With two or more stages and no limiter, the step prologue (sensor, wiggle source, CFL speeds of
 // u^n) is folded into the first stage kernel, which then stores L(u^n) unscaled because dt is not
-// known yet; the dt reduction runs right after it and the second stage scales the stored first
-// delta by its Runge-Kutta coefficient times dt.
+// known yet; the second stage starts with the dt reduction of the first stage's per-CTA maxima
+// and scales the stored first delta by its Runge-Kutta coefficient times dt.
 int enqueue_step(dg_t *h, double dt, cudaEvent_t *ev = nullptr)
 {
     const Schedule S = schedule_for(stage_count(h));
@@ -559,10 +559,17 @@ int enqueue_step(dg_t *h, double dt, cudaEvent_t *ev = nullptr)
         if (ev) CK(h, cudaEventRecord(ev[ne++], h->stream));
     }
     const int c = h->cur, nx = 1 - h->cur;
+    int grid1 = 0;  // grid of the first stage: the number of per-CTA maxima the second reduces
     for (int i = 0; i < S.stages; ++i) {
         const StageDesc &d = S.s[i];
         StageArgs a;
         fill_stage_args(h, S, i, c, fused, a);
+        if (fused && i == 1) {
+            // the dt reduction runs at the start of the second stage
+            a.dt_partial = h->partial;
+            a.dt_nblk = grid1;
+            a.dt_fixed = dt > 0.0 ? dt : 0.0;
+        }
         int grid = 0;
         CK(h, launch_stage_any(h, a, &grid));
         if (h->p.positivity_on) {
@@ -581,10 +588,7 @@ int enqueue_step(dg_t *h, double dt, cudaEvent_t *ev = nullptr)
         if (ev) CK(h, cudaEventRecord(ev[ne++], h->stream));
         if (fused && i == 0) {
             if (grid > h->partial_cap) return fail(h, DG_EINVAL, "stage grid %d exceeds %d", grid, h->partial_cap);
-            dt_kernel<<<1, 256, 0, h->stream>>>(h->partial, grid, dt > 0.0 ? dt : 0.0, h->p.cfl, h->hmin,
-                                                h->degree + 1, h->dtp, 1, h->status);
-            CK(h, cudaGetLastError());
-            if (ev) CK(h, cudaEventRecord(ev[ne++], h->stream));
+            grid1 = grid;
         }
     }
     h->fused_last = fused ? 1 : 0;
@@ -906,11 +910,11 @@ int dg_step_timed(dg_t *h, double dt, float *ms, int nms)
     const int o = h->forced_last ? 1 : 0;
     const float fms = h->forced_last ? d[0] : 0.0f;
     if (h->fused_last) {
-        // launch order: stage 1 (with the prologue work), dt reduction, stages 2..s
+        // launch order: stage 1 (with the prologue work), stages 2..s (the second starts with the
+        // dt reduction, so there is no separate dt launch)
         ms[0] = fms;
-        ms[2] = d[o];
-        ms[1] = d[o + 1];
-        for (int i = 1; i < ns; ++i) ms[2 + i] = d[o + 1 + i];
+        ms[1] = 0.0f;
+        for (int i = 0; i < ns; ++i) ms[2 + i] = d[o + i];
     } else {
         for (int i = 0; i < nl; ++i) ms[i] = d[o + i];
         ms[0] += fms;

@@ -99,6 +99,12 @@ struct StageArgs {
     int din_dt;
     double din_coef;
     double cfl;  // CFL factor (read by the batched time-step kernel)
+    // second stage of a step with the prologue folded in: every CTA computes the step's dt from
+    // the first stage's per-CTA maxima dt_partial[dt_nblk][2] (or takes dt_fixed > 0); CTA 0
+    // publishes it to dtp {dt, step + 1, t + dt}
+    const double *dt_partial;
+    int dt_nblk;
+    double dt_fixed;
 
     // per-simulation constants of the stage body in both precisions, derived on the host from the
     // fields above by stage_consts() (FP64 divisions inside the tile loop are costly on this part)

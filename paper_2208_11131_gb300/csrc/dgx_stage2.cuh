@@ -192,6 +192,43 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
     }
     if (tid == 0) s_status = 0;
 
+    // time step of the step from the first stage's per-CTA maxima (Eq. timestep), identical in
+    // every CTA (maxima are exact in any order)
+    __shared__ double s_dt;
+    if (!BATCH && A0->dt_partial) {
+        double c = 0.0, v = 0.0;
+        for (int i = tid; i < A0->dt_nblk; i += nth) {
+            c = fmax(c, A0->dt_partial[2 * i]);
+            v = fmax(v, A0->dt_partial[2 * i + 1]);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            c = fmax(c, __shfl_xor_sync(0xffffffffu, c, off));
+            v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+        }
+        if ((tid & 31) == 0) {
+            s_red[0][tid >> 5] = c;
+            s_red[1][tid >> 5] = v;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < nth / 32; ++w) {
+                c = fmax(c, s_red[0][w]);
+                v = fmax(v, s_red[1][w]);
+            }
+            const double dt = A0->dt_fixed > 0.0 ? A0->dt_fixed : A0->cfl * A0->hmin / (2.0 * (N + 1) * (c + v));
+            s_dt = dt;
+            if (blockIdx.x == 0) {
+                if (!(dt > 0.0) || !isfinite(dt)) atomicOr(A0->status, DG_STATUS_BADDT);
+                double *dtp = const_cast<double *>(A0->dtp);
+                dtp[0] = dt;
+                dtp[1] += 1.0;
+                dtp[2] += dt;
+            }
+        }
+        __syncthreads();
+    }
+
     auto tile_origin = [&](const StageArgs &T, int tile, int *o, int *V) {
         int b = tile;
         const int tx = b % T.ntile[0];
@@ -288,8 +325,9 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
             cax[a] = K[SK_CAX + a];
         }
         const Real src_w = (Real)(DIM == 2 ? 0.25 : 0.125);
-        const Real dt = A.epi_unit_dt ? Real(1) : ((A.mode != 0 && A.dtp) ? (Real)A.dtp[0] : Real(0));
-        const Real dsc = A.din_dt ? (Real)(A.din_coef * A.dtp[0]) : Real(1);  // stored delta -> true delta
+        const double dstep = (!BATCH && A.dt_partial) ? s_dt : (A.dtp ? A.dtp[0] : 0.0);
+        const Real dt = A.epi_unit_dt ? Real(1) : (A.mode != 0 ? (Real)dstep : Real(0));
+        const Real dsc = A.din_dt ? (Real)(A.din_coef * dstep) : Real(1);  // stored delta -> true delta
         const Real ca = K[SK_CA], cx = K[SK_CX], cb = K[SK_CB];
         const Real za = K[SK_ZA], zx = K[SK_ZX], zb = K[SK_ZB];
         Real *xb = static_cast<Real *>(A.xbuf);
