@@ -38,11 +38,14 @@ __device__ __forceinline__ void cp_async_4(void *smem, const void *gmem)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-constexpr int kStageThreads = 256;  // threads of every stage-kernel CTA
-
 template <int DIM, int N, typename Real, bool AV, bool NS, int TX, int TY, int TZ, bool PF>
 struct Stage2Plan {
     using S = Shape<DIM, N, TX, TY, TZ>;
+    // threads per CTA and the resident CTAs per SM the registers are bounded for: 2-D FP32 tiles
+    // balance their phases better over 10 warps (the face points of an 8x4 or 4x8 tile, 304,
+    // fit one round), measured faster at every degree; the rest uses 8 warps
+    static constexpr int NTH = (DIM == 2 && sizeof(Real) == 4) ? 320 : 256;
+    static constexpr int MINB = (DIM == 2 && sizeof(Real) == 4) ? 2 : 1;
     static constexpr int Q = S::Q, NP = S::NP, NPF = S::NPF, NC = S::NC;
     static constexpr int NF = NC + (AV ? 1 : 0);
     static constexpr int TC = S::TC, NSLOT = S::NSLOT, NFACE = S::NFACE;
@@ -152,15 +155,15 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
     Real *tLp = tG + Q, *tLm = tLp + Q, *tCm = tLm + Q, *tCp = tCm + Q, *tDm = tCp + Q, *tDp = tDm + Q;
     Real *sIn0 = sm + PL::OFF_IN0, *sIn1 = sm + PL::OFF_IN1, *sU = sm + PL::OFF_U, *sF = sm + PL::OFF_F;
     Real *sR = sm + PL::OFF_R, *sUt = sm + PL::OFF_UT, *sFh = sm + PL::OFF_FH, *sWig = sm + PL::OFF_WIG;
-    __shared__ double s_red[2][8];
+    __shared__ double s_red[2][PL::NTH / 32];
     int *sGa = reinterpret_cast<int *>(sm + PL::NREAL);
     int *sGb = sGa + NSLOT;
     __shared__ int s_status;
 
-    // every launch uses kStageThreads threads: loop strides are compile-time constants, so the
+    // every launch uses PL::NTH threads: loop strides are compile-time constants, so the
     // per-thread loops unroll and their index arithmetic folds
     const int tid = threadIdx.x;
-    constexpr int nth = kStageThreads;
+    constexpr int nth = PL::NTH;
     const int ntiles = BATCH ? tile_off[nsims] : A0->ntile[0] * A0->ntile[1] * A0->ntile[2];
     // simulation of a work-list tile (binary search in the prefix sums)
     auto sim_of = [&](int tile) -> int {
@@ -879,13 +882,16 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
 }
 
 template <int DIM, int N, typename Real, bool AV, bool NS, int TX, int TY, int TZ, bool PF>
-__global__ void __launch_bounds__(kStageThreads) stage2_kernel(const StageArgs A, const Tables<Real> Tg)
+__global__ void __launch_bounds__(Stage2Plan<DIM, N, Real, AV, NS, TX, TY, TZ, PF>::NTH,
+                                  Stage2Plan<DIM, N, Real, AV, NS, TX, TY, TZ, PF>::MINB)
+    stage2_kernel(const StageArgs A, const Tables<Real> Tg)
 {
     stage2_body<DIM, N, Real, AV, NS, TX, TY, TZ, PF, false>(&A, nullptr, nullptr, 1, Tg);
 }
 
 template <int DIM, int N, typename Real, bool AV, bool NS, int TX, int TY, int TZ, bool PF>
-__global__ void __launch_bounds__(kStageThreads)
+__global__ void __launch_bounds__(Stage2Plan<DIM, N, Real, AV, NS, TX, TY, TZ, PF>::NTH,
+                                  Stage2Plan<DIM, N, Real, AV, NS, TX, TY, TZ, PF>::MINB)
     stage2_batch_kernel(const StageArgs *descs, const int *tile_off, int nsims, const Tables<Real> Tg)
 {
     stage2_body<DIM, N, Real, AV, NS, TX, TY, TZ, PF, true>(nullptr, descs, tile_off, nsims, Tg);
@@ -909,7 +915,7 @@ cudaError_t run_stage2(const StageArgs &a, const Tables<Real> &t, cudaStream_t s
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k, kStageThreads, PL::BYTES);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k, PL::NTH, PL::BYTES);
         if (e != cudaSuccess) return e;
         if (blocks_per_sm < 1) blocks_per_sm = 1;
     }
@@ -917,7 +923,7 @@ cudaError_t run_stage2(const StageArgs &a, const Tables<Real> &t, cudaStream_t s
     if (tiles == 0) return cudaSuccess;
     const int grid = tiles < sms * blocks_per_sm ? tiles : sms * blocks_per_sm;
     if (grid_out) *grid_out = grid;
-    k<<<grid, kStageThreads, PL::BYTES, s>>>(a, t);
+    k<<<grid, PL::NTH, PL::BYTES, s>>>(a, t);
     return cudaGetLastError();
 }
 
@@ -939,13 +945,13 @@ cudaError_t run_stage2_batch(const StageArgs *descs, const int *tile_off, int ns
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k, kStageThreads, PL::BYTES);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k, PL::NTH, PL::BYTES);
         if (e != cudaSuccess) return e;
         if (blocks_per_sm < 1) blocks_per_sm = 1;
     }
     if (total_tiles == 0) return cudaSuccess;
     const int grid = total_tiles < sms * blocks_per_sm ? total_tiles : sms * blocks_per_sm;
-    k<<<grid, kStageThreads, PL::BYTES, s>>>(descs, tile_off, nsims, t);
+    k<<<grid, PL::NTH, PL::BYTES, s>>>(descs, tile_off, nsims, t);
     return cudaGetLastError();
 }
 
