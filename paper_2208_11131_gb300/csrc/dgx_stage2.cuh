@@ -41,10 +41,11 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <int DIM, int N, typename Real, bool AV, bool NS, int TX, int TY, int TZ, bool PF>
 struct Stage2Plan {
     using S = Shape<DIM, N, TX, TY, TZ>;
-    // threads per CTA and the resident CTAs per SM the registers are bounded for: 2-D FP32 tiles
-    // balance their phases better over 10 warps (the face points of an 8x4 or 4x8 tile, 304,
-    // fit one round), measured faster at every degree; the rest uses 8 warps
-    static constexpr int NTH = (DIM == 2 && sizeof(Real) == 4) ? 320 : 256;
+    // threads per CTA and the resident CTAs per SM the registers are bounded for (measured at
+    // every degree): 2-D FP32 tiles balance their phases better over 10 warps (the 304 face
+    // points of an 8x4 or 4x8 tile fit one round), 2 CTAs per SM; a 3-D FP32 tile fills most of
+    // the shared memory, so one CTA per SM runs 16 warps to hide latency; FP64 uses 8 warps
+    static constexpr int NTH = sizeof(Real) == 4 ? (DIM == 2 ? 320 : 512) : 256;
     static constexpr int MINB = (DIM == 2 && sizeof(Real) == 4) ? 2 : 1;
     static constexpr int Q = S::Q, NP = S::NP, NPF = S::NPF, NC = S::NC;
     static constexpr int NF = NC + (AV ? 1 : 0);
