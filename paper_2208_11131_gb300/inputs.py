@@ -83,6 +83,12 @@ class Workload:
 
 # ------------------------------------------------------------------ the five paper-shaped workloads
 
+def isentropic_vortex(N: int = 32, n: int = 3) -> Workload:
+    """2-D Euler isentropic vortex of Sec. 5.1: periodic [-5,5]^2, gamma=1.4, beta=5 (steady)."""
+    return Workload("isentropic_vortex_2d", 2, n, (N, N, 1), (-5.0, -5.0, 0.0), (5.0, 5.0, 1.0), gamma=1.4,
+                    cfl=0.3, steps=100)
+
+
 def c1_density_wave(N: int = 32, n: int = 2) -> Workload:
     """2-D Euler, gamma=5/3, periodic [0,1]^2, rho = 1 + 0.2 sin 2pi(x+y), v=(1,1), P=1."""
     return Workload("density_wave_2d", 2, n, (N, N, 1), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), gamma=5.0 / 3.0,
@@ -168,6 +174,25 @@ def density_wave_ic(wl: Workload, t: float = 0.0):
         rho = 1.0 + 0.2 * np.sin(2.0 * np.pi * (x + y - 2.0 * t))
         one = np.ones_like(x)
         return _cons(wl.gamma, rho, [one, one], one, np.zeros_like(x) if wl.av_on else None)
+    return f
+
+
+def isentropic_vortex_ic(wl: Workload, beta: float = 5.0):
+    """the vortex of Sec. 5.1 (Yee's original set-up, background rho = p = 1) centred at the origin:
+    v = beta/(2 pi) e^((1-r^2)/2) (-y, x), specific internal energy
+    u = 1/(gamma-1) - beta^2/(8 gamma pi^2) e^(1-r^2), rho = ((gamma-1) u)^(1/(gamma-1)),
+    p = (gamma-1) rho u; isentropic (p = rho^gamma) and in radial balance dp/dr = rho v^2/r, so it is
+    also the exact solution at every time"""
+    g = wl.gamma
+
+    def f(X):
+        x, y = X[:, 0], X[:, 1]
+        r2 = x * x + y * y
+        a = beta / (2.0 * np.pi) * np.exp(0.5 * (1.0 - r2))
+        u = 1.0 / (g - 1.0) - beta * beta / (8.0 * g * np.pi ** 2) * np.exp(1.0 - r2)
+        rho = ((g - 1.0) * u) ** (1.0 / (g - 1.0))
+        p = (g - 1.0) * rho * u
+        return _cons(g, rho, [-a * y, a * x], p, np.zeros_like(x) if wl.av_on else None)
     return f
 
 
