@@ -56,6 +56,7 @@ class Cfg(ctypes.Structure):
         ("positivity_on", ctypes.c_int), ("cfl", ctypes.c_double), ("rk_stages", ctypes.c_int),
         ("forcing_on", ctypes.c_int), ("force_amp", ctypes.c_double), ("force_ts", ctypes.c_double),
         ("force_dt", ctypes.c_double), ("force_seed", ctypes.c_ulonglong),
+        ("tracer_on", ctypes.c_int), ("eta", ctypes.c_double),
     ]
 
 FMODES = 16  # forcing-state mode stride
@@ -88,6 +89,7 @@ def lib():
             "or_forcing_uniform": (D, [ctypes.c_ulonglong, ctypes.c_ulonglong]),
             "or_forcing_normal": (D, [ctypes.c_ulonglong, ctypes.c_ulonglong]),
             "or_forcing_update": (I, [C, P, D]), "or_forcing_eval": (I, [C, P, I, P, P]),
+            "or_hllc_tracer": (I, [I, I, D, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -130,10 +132,13 @@ def recovery_matrices(n: int, f: float | None = None):
 
 
 def hllc(dim: int, axis: int, gamma: float, uL, uR):
+    """HLLC flux of the Euler fields; with d+3 components the last is a passive tracer rho c"""
     uL = np.ascontiguousarray(uL, dtype=np.float64)
     uR = np.ascontiguousarray(uR, dtype=np.float64)
-    F = np.zeros(dim + 2)
-    st = lib().or_hllc(dim, axis, gamma, _p(uL), _p(uR), _p(F))
+    tr = uL.size == dim + 3
+    F = np.zeros(dim + 2 + tr)
+    fn = lib().or_hllc_tracer if tr else lib().or_hllc
+    st = fn(dim, axis, gamma, _p(uL), _p(uR), _p(F))
     return F, st
 
 
@@ -201,6 +206,8 @@ class Problem:
     force_ts: float = 1.0
     force_dt: float = 0.01
     force_seed: int = 0
+    tracer_on: int = 0
+    eta: float = 0.0
 
     def cfg(self) -> Cfg:
         c = Cfg()
@@ -218,6 +225,7 @@ class Problem:
         c.forcing_on, c.force_amp, c.force_ts, c.force_dt = (int(self.forcing_on), self.force_amp, self.force_ts,
                                                              self.force_dt)
         c.force_seed = int(self.force_seed) & 0xFFFFFFFFFFFFFFFF
+        c.tracer_on, c.eta = int(self.tracer_on), float(self.eta)
         return c
 
     @property
@@ -230,7 +238,7 @@ class Problem:
 
     @property
     def nfields(self) -> int:
-        return self.dim + 2 + (1 if self.av_on else 0)
+        return self.dim + 2 + (1 if self.tracer_on else 0) + (1 if self.av_on else 0)
 
     @property
     def h(self):

@@ -63,7 +63,7 @@
 
 #define OR_MAXN 7
 #define OR_MAXQ (OR_MAXN + 1)
-#define OR_MAXF 6
+#define OR_MAXF 7
 
 /* status codes (shared meaning with the test suite only) */
 #define OR_OK 0
@@ -86,6 +86,9 @@ typedef struct {
     int forcing_on;
     double force_amp, force_ts, force_dt;
     unsigned long long force_seed;
+    /* passive tracer (Sec. 3.4): conserved field rho c after the energy, diffusivity eta */
+    int tracer_on;
+    double eta;
 } or_cfg;
 
 /* ------------------------------------------------------------------ */
@@ -367,27 +370,34 @@ static int to_prim(const double *u, int d, double g, or_prim *P)
     return 0;
 }
 
-/* Euler flux along axis ax, Eq. flux_matrix */
-static void euler_flux(const double *u, const or_prim *P, int d, int ax, double *F)
+/* Euler flux along axis ax, Eq. flux_matrix; with a tracer (tr = 1) its row c rho v_ax (Sec. 3.4) */
+static void euler_flux_tr(const double *u, const or_prim *P, int d, int tr, int ax, double *F)
 {
     double vn = P->v[ax];
     F[0] = u[0] * vn;
     for (int b = 0; b < d; ++b) F[1 + b] = u[1 + b] * vn + (b == ax ? P->p : 0.0);
     F[d + 1] = (P->e + P->p) * vn;
+    if (tr) F[d + 2] = u[d + 2] * vn;
 }
 
-/* HLLC flux along axis ax (Toro), Davis wave-speed estimates. */
-int or_hllc(int d, int ax, double g, const double *uL, const double *uR, double *F)
+static void euler_flux(const double *u, const or_prim *P, int d, int ax, double *F)
+{
+    euler_flux_tr(u, P, d, 0, ax, F);
+}
+
+/* HLLC flux along axis ax (Toro), Davis wave-speed estimates; a passive tracer (tr = 1) is carried
+ * in the star states with the concentration of its side, c_K rho*_K */
+static int hllc_tr(int d, int tr, int ax, double g, const double *uL, const double *uR, double *F)
 {
     or_prim L, R;
     int bad = to_prim(uL, d, g, &L) | to_prim(uR, d, g, &R);
-    int nf = d + 2;
+    int nf = d + 2 + tr;
     double vL = L.v[ax], vR = R.v[ax];
     double SL = fmin(vL - L.cs, vR - R.cs);
     double SR = fmax(vL + L.cs, vR + R.cs);
     double FL[OR_MAXF], FR[OR_MAXF];
-    euler_flux(uL, &L, d, ax, FL);
-    euler_flux(uR, &R, d, ax, FR);
+    euler_flux_tr(uL, &L, d, tr, ax, FL);
+    euler_flux_tr(uR, &R, d, tr, ax, FR);
     if (SL >= 0.0) {
         for (int f = 0; f < nf; ++f) F[f] = FL[f];
         return bad;
@@ -413,15 +423,28 @@ int or_hllc(int d, int ax, double g, const double *uL, const double *uR, double 
     us[0] = fac;
     for (int b = 0; b < d; ++b) us[1 + b] = fac * (b == ax ? Ss : K->v[b]);
     us[d + 1] = fac * (K->e / K->rho + (Ss - vK) * (Ss + K->p / (K->rho * (SK - vK))));
+    if (tr) us[d + 2] = fac * (uK[d + 2] / K->rho);
     for (int f = 0; f < nf; ++f) F[f] = FK[f] + SK * (us[f] - uK[f]);
     return bad;
 }
 
-/* Navier-Stokes flux along axis ax from the state u and its physical
- * gradient grad[beta][field] (Sec. 3.3).  Returns nonzero if rho <= 0. */
-int or_ns_flux(int d, int ax, double g, double nu, double kappa, const double *u, const double *grad, double *F)
+int or_hllc(int d, int ax, double g, const double *uL, const double *uR, double *F)
 {
-    int nf = d + 2;
+    return hllc_tr(d, 0, ax, g, uL, uR, F);
+}
+
+int or_hllc_tracer(int d, int ax, double g, const double *uL, const double *uR, double *F)
+{
+    return hllc_tr(d, 1, ax, g, uL, uR, F);
+}
+
+/* Navier-Stokes flux along axis ax from the state u and its physical
+ * gradient grad[beta][field] (Sec. 3.3); with a tracer (tr = 1) its diffusion row
+ * eta rho d_ax c = eta (d_ax (rho c) - c d_ax rho) (Sec. 3.4).  Returns nonzero if rho <= 0. */
+static int ns_flux_tr(int d, int tr, int ax, double g, double nu, double kappa, double eta, const double *u,
+                      const double *grad, double *F)
+{
+    int nf = d + 2 + tr;
     double rho = u[0];
     if (!(rho > 0.0)) return 1;
     double v[3] = {0, 0, 0};
@@ -444,7 +467,13 @@ int or_ns_flux(int d, int ax, double g, double nu, double kappa, const double *u
         work += v[b] * Pi[b];
     }
     F[d + 1] = work + kappa * (g - 1.0) * rho * duint;
+    if (tr) F[d + 2] = eta * (grad[ax * nf + d + 2] - (u[d + 2] / rho) * grad[ax * nf + 0]);
     return 0;
+}
+
+int or_ns_flux(int d, int ax, double g, double nu, double kappa, const double *u, const double *grad, double *F)
+{
+    return ns_flux_tr(d, 0, ax, g, nu, kappa, 0.0, u, grad, F);
 }
 
 static double clip01(double a) { return a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a); }
@@ -454,12 +483,13 @@ static double clip01(double a) { return a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a); }
 /* ------------------------------------------------------------------ */
 
 typedef struct {
-    int d, n, Q, M, NF, FT, IA;
+    int d, n, Q, M, NF, FT, IA, TR;
     long ncell;
     int N[3];
     double h[3], hmin;
     int P;
     int need_grad;
+    int diss; /* physical diffusive fluxes: NS (nu, kappa) and/or tracer diffusion (eta) */
 } or_geo;
 
 static void geo_init(or_geo *g, const or_cfg *c)
@@ -478,11 +508,13 @@ static void geo_init(or_geo *g, const or_cfg *c)
         g->h[a] = (c->hi[a] - c->lo[a]) / c->N[a];
         if (g->h[a] < g->hmin) g->hmin = g->h[a];
     }
-    g->NF = c->dim + 2;
+    g->TR = c->tracer_on ? 1 : 0;
+    g->NF = c->dim + 2 + g->TR;
     g->FT = g->NF + (c->av_on ? 1 : 0);
     g->IA = g->NF;
     g->P = c->n + 1;
-    g->need_grad = c->av_on || c->nu > 0.0 || c->kappa > 0.0;
+    g->diss = c->nu > 0.0 || c->kappa > 0.0 || (g->TR && c->eta > 0.0);
+    g->need_grad = c->av_on || g->diss;
 }
 
 static long cell_index(const or_geo *g, const int *ci)
@@ -511,6 +543,7 @@ static int check_cfg(const or_cfg *c)
     if (!(c->gamma > 1.0)) return OR_EINVAL;
     if (c->forcing_on && (!(c->force_ts > 0.0) || !(c->force_dt > 0.0) || !(c->force_amp >= 0.0)))
         return OR_EINVAL;
+    if (c->tracer_on && !(c->eta >= 0.0)) return OR_EINVAL;
     return OR_OK;
 }
 
@@ -737,7 +770,7 @@ static int face_flux(const or_cfg *c, const or_tab *T, const or_geo *g, const do
             or_prim P;
             face_trace(T, g, w, K, ax, s, k, NF, u);
             if (to_prim(u, d, c->gamma, &P)) status = OR_ENONPHYS;
-            euler_flux(u, &P, d, ax, Fh + k * NF);
+            euler_flux_tr(u, &P, d, g->TR, ax, Fh + k * NF);
         }
         return status;
     }
@@ -746,9 +779,9 @@ static int face_flux(const or_cfg *c, const or_tab *T, const or_geo *g, const do
     for (int k = 0; k < NQF; ++k) {
         face_trace(T, g, w, KL, ax, 1, k, FT, uL[k]);
         face_trace(T, g, w, KR, ax, 0, k, FT, uR[k]);
-        if (or_hllc(d, ax, c->gamma, uL[k], uR[k], Fh + k * NF)) status = OR_ENONPHYS;
+        if (hllc_tr(d, g->TR, ax, c->gamma, uL[k], uR[k], Fh + k * NF)) status = OR_ENONPHYS;
     }
-    int ns = c->nu > 0.0 || c->kappa > 0.0;
+    int ns = g->diss;
     if (!ns && !c->av_on) return status;
     double ut[OR_MAXQ * OR_MAXQ * OR_MAXF];
     double gt[OR_MAXQ * OR_MAXQ * 3 * OR_MAXF];
@@ -761,7 +794,8 @@ static int face_flux(const or_cfg *c, const or_tab *T, const or_geo *g, const do
             double grad[3 * OR_MAXF];
             for (int b = 0; b < d; ++b)
                 for (int f = 0; f < NF; ++f) grad[b * NF + f] = gt[(k * 3 + b) * NF + f];
-            if (or_ns_flux(d, ax, c->gamma, c->nu, c->kappa, ut + k * NF, grad, Fd)) status = OR_ENONPHYS;
+            if (ns_flux_tr(d, g->TR, ax, c->gamma, c->nu, c->kappa, c->eta, ut + k * NF, grad, Fd))
+                status = OR_ENONPHYS;
         }
         if (c->av_on) {
             or_prim PL, PR;
@@ -790,7 +824,7 @@ int or_rhs_forced(const or_cfg *c, const double *w, const double *wig, const dou
     int status = OR_OK;
     double two1d = ldexp(1.0, 1 - d), two_d = ldexp(1.0, -d);
     memset(rhs, 0, sizeof(double) * (size_t)FT * g.ncell * M);
-    int ns = c->nu > 0.0 || c->kappa > 0.0;
+    int ns = g.diss;
 
     /* volume integral and alpha source (per cell) */
 #pragma omp parallel for schedule(static) reduction(| : status)
@@ -817,10 +851,10 @@ int or_rhs_forced(const or_cfg *c, const double *w, const double *wig, const dou
             double eps = c->av_on ? av_eps(c, &g, u[g.IA], P.cs) : 0.0;
             double Fx[3][OR_MAXF];
             for (int ax = 0; ax < d; ++ax) {
-                euler_flux(u, &P, d, ax, Fx[ax]);
+                euler_flux_tr(u, &P, d, g.TR, ax, Fx[ax]);
                 if (ns) {
                     double Fn[OR_MAXF];
-                    or_ns_flux(d, ax, c->gamma, c->nu, c->kappa, u, grad, Fn);
+                    ns_flux_tr(d, g.TR, ax, c->gamma, c->nu, c->kappa, c->eta, u, grad, Fn);
                     for (int f = 0; f < NF; ++f) Fx[ax][f] -= Fn[f];
                 }
                 if (c->av_on)

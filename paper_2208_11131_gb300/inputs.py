@@ -48,6 +48,9 @@ class Workload:
     force_ts: float = 1.0
     force_dt: float = 0.01
     force_seed: int = 0
+    # passive tracer (Sec. 3.4): conserved field rho c after the energy, diffusivity eta
+    tracer_on: int = 0
+    eta: float = 0.0
 
     @property
     def ncell(self) -> int:
@@ -59,11 +62,11 @@ class Workload:
 
     @property
     def nfields(self) -> int:
-        return self.dim + 2 + (1 if self.av_on else 0)
+        return self.ncons + (1 if self.av_on else 0)
 
     @property
     def ncons(self) -> int:
-        return self.dim + 2
+        return self.dim + 2 + (1 if self.tracer_on else 0)
 
     @property
     def dofs(self) -> int:
@@ -87,6 +90,13 @@ def isentropic_vortex(N: int = 32, n: int = 3) -> Workload:
     """2-D Euler isentropic vortex of Sec. 5.1: periodic [-5,5]^2, gamma=1.4, beta=5 (steady)."""
     return Workload("isentropic_vortex_2d", 2, n, (N, N, 1), (-5.0, -5.0, 0.0), (5.0, 5.0, 1.0), gamma=1.4,
                     cfl=0.3, steps=100)
+
+
+def gaussian_pulse(N: int = 16, n: int = 2) -> Workload:
+    """2-D diffusion of a Gaussian tracer pulse (Sec. 5.2): gas at rest (rho = p = 1, gamma = 1.4) on
+    the periodic [-0.5,0.5]^2, tracer diffusivity eta = 1/128."""
+    return Workload("gaussian_pulse_2d", 2, n, (N, N, 1), (-0.5, -0.5, 0.0), (0.5, 0.5, 1.0), gamma=1.4, cfl=0.3,
+                    steps=100, tracer_on=1, eta=1.0 / 128.0)
 
 
 def c1_density_wave(N: int = 32, n: int = 2) -> Workload:
@@ -193,6 +203,26 @@ def isentropic_vortex_ic(wl: Workload, beta: float = 5.0):
         rho = ((g - 1.0) * u) ** (1.0 / (g - 1.0))
         p = (g - 1.0) * rho * u
         return _cons(g, rho, [-a * y, a * x], p, np.zeros_like(x) if wl.av_on else None)
+    return f
+
+
+def gaussian_pulse_ic(wl: Workload, t: float, c_b: float = 0.1, c_g: float = 1.0):
+    """exact tracer field of Sec. 5.2 at time t: c = c_b + sum_j c_g/(2 pi s^2) exp(-|x-j|^2/(2 s^2)),
+    s^2 = 2 eta t, summed over the periodic images j of the unit box; gas at rest, rho = p = 1"""
+    s2 = 2.0 * wl.eta * t
+
+    def f(X):
+        x, y = X[:, 0], X[:, 1]
+        c = np.full_like(x, c_b)
+        for jx in range(-4, 5):
+            for jy in range(-4, 5):
+                c += c_g / (2.0 * np.pi * s2) * np.exp(-((x - jx) ** 2 + (y - jy) ** 2) / (2.0 * s2))
+        one = np.ones_like(x)
+        zero = np.zeros_like(x)
+        fields = [one, zero, zero, one / (wl.gamma - 1.0), c]
+        if wl.av_on:
+            fields.append(zero)
+        return np.stack(fields)
     return f
 
 

@@ -423,3 +423,34 @@ def test_av_defaults_golden():
     assert (P.av_scale, P.f_v, P.f_tau, P.f_w, P.s_onset) == tuple(
         float(vals[k]) for k in ("av_scale", "f_v", "f_tau", "f_w", "s_onset"))
     assert P.cfl == float(vals["cfl"])
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+def test_recovery_is_the_l2_projection_of_discontinuous_data(n):
+    """Sec. 3.2 by brute force: the L2 projection of the two cells' (discontinuous, random) data
+    onto Legendre polynomials of degree n+1 on K* (f h on each side), by dense Gauss quadrature split
+    at the interface, gives the recovered value and normal derivative at the interface."""
+    from numpy.polynomial import legendre as L
+    rng = np.random.default_rng(30 + n)
+    hx, hy = 0.7, 0.4
+    P = oracle.Problem(dim=2, n=n, N=(2, 1), hi=(2 * hx, hy))
+    w = rng.normal(size=P.shape())
+    ut, gt = oracle.face_recovery(P, w, 0, 1, 0)
+    f = 0.75 if n <= 2 else 1.0
+    Q = n + 1
+    yg, _ = L.leggauss(Q)
+    xq, wq = L.leggauss(60)
+    Pt = lambda l, x: math.sqrt(2 * l + 1) * L.legval(x, [0] * l + [1])
+    sl, sr = 0.5 * (xq - 1), 0.5 * (xq + 1)  # K* coordinate on [-1,0] and [0,1]
+    for k in range(Q):
+        for fld in range(P.dim + 2):
+            def side(c, xi):
+                return sum(w[fld, c, lx + Q * ly] * Pt(lx, xi) * Pt(ly, yg[k]) for ly in range(Q) for lx in range(Q))
+            # physical offset from the interface x = s f hx: cell 0 at xi = 1 + 2 f s, cell 1 at xi = -1 + 2 f s
+            q = []
+            for l in range(n + 2):
+                Pl = L.legval(sl, [0] * l + [1]), L.legval(sr, [0] * l + [1])
+                integ = 0.5 * np.sum(wq * side(0, 1 + 2 * f * sl) * Pl[0]) + 0.5 * np.sum(wq * side(1, -1 + 2 * f * sr) * Pl[1])
+                q.append(integ * (2 * l + 1) / 2)
+            assert abs(L.legval(0.0, q) - ut[k, fld]) < 1e-12
+            assert abs(L.legval(0.0, L.legder(q)) / (f * hx) - gt[k, 0, fld]) < 1e-11
