@@ -12,7 +12,7 @@
  * State layout (host and device, all entry points): float64
  *   w[field][cell][mode],  cell = ix + Nx*(iy + Ny*iz),
  *   mode l = lx + (n+1)*(ly + (n+1)*lz),
- *   fields (rho, rho vx, rho vy, [rho vz], e, [alpha]).
+ *   fields (rho, rho vx, rho vy, [rho vz], e, [rho c], [alpha]) -- rho c with the tracer on.
  * w[f][K][0] is the cell mean (basis normalised so that (1/|K|) int phi_l phi_m = delta).
  *
  * Ownership: the library owns every device buffer of a handle (allocated in
@@ -90,7 +90,13 @@ typedef struct dg_grid {
  *             rho s enters the momentum and s.(rho v) the energy, integrated
  *             with the volume Gauss rule.  Each step applies the updates due at
  *             its start time and keeps that field for all of its stages.
- *             Defaults: off, force_amp 0, force_ts 1, force_dt 0.01, seed 0. */
+ *             Defaults: off, force_amp 0, force_ts 1, force_dt 0.01, seed 0.
+ *  tracer_on: 1 adds a passive tracer (Sec. 3.4): the conserved field rho c
+ *             right after the energy (before alpha), advected with flux
+ *             c rho v and diffused with flux tracer_eta rho grad c through the
+ *             recovered gradients of Sec. 3.2; it has no effect on the flow.
+ *             Changing it reallocates the state (one more field).  Not
+ *             supported in batches. */
 typedef struct dg_params {
     int precision;
     int rk_stages;
@@ -101,6 +107,8 @@ typedef struct dg_params {
     int forcing_on;
     double force_amp, force_ts, force_dt;
     unsigned long long force_seed;
+    int tracer_on;
+    double tracer_eta;
 } dg_params;
 
 /* Fill p with the defaults listed above (DG_FP64, automatic RK, AV off). */

@@ -321,6 +321,7 @@ int prepare_kernels(dg_t *h);
 int alloc_buffers(dg_t *h)
 {
     free_buffers(h);
+    h->nc = h->dim + 2 + (h->p.tracer_on ? 1 : 0);
     h->nf = h->nc + (h->p.av_on ? 1 : 0);
     h->nw = (size_t)h->nf * h->ncell * h->M;
     const size_t rs = real_size(h);
@@ -396,6 +397,8 @@ void base_stage_args(const dg_t *h, StageArgs &a)
     a.nu = h->nu;
     a.kappa = h->kappa;
     a.ns_on = (h->nu > 0.0 || h->kappa > 0.0) ? 1 : 0;
+    a.tracer_on = h->p.tracer_on;
+    a.eta = h->p.tracer_eta;
     a.av_on = h->p.av_on;
     a.av_scale = h->p.av_scale;
     a.f_v = h->p.f_v;
@@ -472,6 +475,7 @@ int prepare_kernels(dg_t *h)
                       : launch_prologue_3d_f64(h->degree, pa, h->td, h->stream));
     LimiterArgs la;
     memset(&la, 0, sizeof la);
+    la.tracer_on = h->p.tracer_on;
     CK(h, launch_limiter_any(h, la));
     return DG_OK;
 }
@@ -545,6 +549,7 @@ int enqueue_step(dg_t *h, double dt, cudaEvent_t *ev = nullptr)
             memset(&la, 0, sizeof la);
             la.ncell = h->ncell;
             la.gamma = h->gamma;
+            la.tracer_on = h->p.tracer_on;
             la.last = 1;
             la.ufull = h->U[h->cur];
             la.uhi = fp32(h) ? h->Uhi[h->cur] : nullptr;
@@ -577,6 +582,7 @@ int enqueue_step(dg_t *h, double dt, cudaEvent_t *ev = nullptr)
             memset(&la, 0, sizeof la);
             la.ncell = h->ncell;
             la.gamma = h->gamma;
+            la.tracer_on = h->p.tracer_on;
             la.last = d.last;
             la.ubase = a.ubase;
             la.delta = d.last ? nullptr : h->D[d.out];
@@ -660,6 +666,8 @@ int dg_default_params(dg_params *p)
     p->force_ts = 1.0;
     p->force_dt = 0.01;
     p->force_seed = 0;
+    p->tracer_on = 0;
+    p->tracer_eta = 0.0;
     return DG_OK;
 }
 
@@ -739,7 +747,10 @@ int dg_set_params(dg_t *h, const dg_params *p)
     if ((p->forcing_on != 0 && p->forcing_on != 1) ||
         (p->forcing_on && (!(p->force_ts > 0.0) || !(p->force_dt > 0.0) || !(p->force_amp >= 0.0))))
         return fail(h, DG_EINVAL, "forcing needs force_ts > 0, force_dt > 0, force_amp >= 0");
-    const bool realloc = p->precision != h->p.precision || p->av_on != h->p.av_on;
+    if ((p->tracer_on != 0 && p->tracer_on != 1) || !(p->tracer_eta >= 0.0))
+        return fail(h, DG_EINVAL, "tracer_on must be 0 or 1 and tracer_eta >= 0");
+    const bool realloc =
+        p->precision != h->p.precision || p->av_on != h->p.av_on || p->tracer_on != h->p.tracer_on;
     h->p = *p;
     if (h->graph) {
         cudaGraphExecDestroy(h->graph);
@@ -1094,7 +1105,7 @@ int dg_batch_create(dg_t *const *sims, int count, dg_batch_t **out)
     for (int k = 0; k < count; ++k) {
         const dg_t *h = sims[k];
         if (!h) return DG_EINVAL;
-        if (h->p.positivity_on || h->p.forcing_on || stage_count(h) < 2) return DG_EUNSUPPORTED;
+        if (h->p.positivity_on || h->p.forcing_on || h->p.tracer_on || stage_count(h) < 2) return DG_EUNSUPPORTED;
         if (h->cur != sims[0]->cur || h->device != sims[0]->device || h->stream != sims[0]->stream)
             return DG_EINVAL;
     }

@@ -25,7 +25,7 @@ namespace dgx {
         return run_stage2_batch_any<DGX_DIM, n, DGX_REAL, sx, sy, sz>(av, ns, descs, tile_off, nsims, total, t, s);
 #define DGX_LIM_CASE(n, sx, sy, sz, px, py, pz) \
     case n:                                    \
-        return run_limiter<DGX_DIM, n, DGX_REAL>(a, t, s);
+        return run_limiter_any<DGX_DIM, n, DGX_REAL>(a, t, s);
 #define DGX_TILE_CASE(n, sx, sy, sz, px, py, pz) \
     case n:                                      \
         st[0] = sx;                              \

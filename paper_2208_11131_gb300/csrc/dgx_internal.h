@@ -49,6 +49,7 @@ enum StageConst {
     SK_GAMMA,
     SK_NU,
     SK_KAPPA,
+    SK_ETA,         // tracer diffusivity (Sec. 3.4)
     SK_CA, SK_CX, SK_CB, SK_ZA, SK_ZX, SK_ZB,  // Runge-Kutta register coefficients
     SK_COUNT
 };
@@ -61,6 +62,8 @@ struct StageArgs {
     double hmin;
     double gamma, nu, kappa;
     int ns_on;  // nu > 0 or kappa > 0
+    int tracer_on;  // passive tracer field rho c after the energy (Sec. 3.4)
+    double eta;     // its diffusivity
     int av_on;
     double av_scale, f_v, f_tau;
     int nf;  // fields incl. alpha
@@ -129,6 +132,7 @@ inline void stage_consts(StageArgs &a, int degree, int dim)
     k[SK_GAMMA] = a.gamma;
     k[SK_NU] = a.nu;
     k[SK_KAPPA] = a.kappa;
+    k[SK_ETA] = a.eta;
     k[SK_CA] = a.ca;
     k[SK_CX] = a.cx;
     k[SK_CB] = a.cb;
@@ -168,6 +172,7 @@ struct LimiterArgs {
     double *ufull;       // FP64 state, limited in place (last stage)
     float *uhi;          // FP32 copy of ufull to refresh (bulk mode, last stage) or null
     int *status;
+    int tracer_on;       // a passive tracer follows the energy: d+3 conserved fields are scaled
 };
 
 struct LaunchCfg {

@@ -110,8 +110,9 @@ __device__ __forceinline__ bool primitives(const Real *u, Real gamma, Real &rho,
     return ok;
 }
 
-// Euler flux along axis a (a may be a run-time value: selected by value, no run-time indexing)
-template <int DIM, typename Real>
+// Euler flux along axis a (a may be a run-time value: selected by value, no run-time indexing);
+// TR: a passive tracer rho c follows the energy, with flux c rho v_a (Sec. 3.4)
+template <int DIM, bool TR = false, typename Real>
 __device__ __forceinline__ void euler_flux(const Real *u, const Real *v, Real p, int a, Real *F)
 {
     Real va = v[0], ma = u[1];
@@ -124,14 +125,17 @@ __device__ __forceinline__ void euler_flux(const Real *u, const Real *v, Real p,
 #pragma unroll
     for (int b = 0; b < DIM; ++b) F[1 + b] = u[1 + b] * va + (b == a ? p : Real(0));
     F[DIM + 1] = (u[DIM + 1] + p) * va;
+    if constexpr (TR) F[DIM + 2] = u[DIM + 2] * va;
 }
 
-// HLLC with Davis wave speeds (Toro); passive transverse momentum.  Returns false on a bad state.
+// HLLC with Davis wave speeds (Toro); passive transverse momentum and (TR) a passive tracer carried
+// in the star state with its side's concentration.  Returns false on a bad state.
 // Written without pointers to local arrays and without early returns: the side values that enter
 // the star state are chosen by value selects, so every array stays in registers.
-template <int DIM, typename Real>
+template <int DIM, bool TR = false, typename Real>
 __device__ __forceinline__ bool hllc(const Real *uL, const Real *uR, Real gamma, int a, Real *F, Real &cL, Real &cR)
 {
+    constexpr int NC = DIM + 2 + (TR ? 1 : 0);
     Real rL, rR, pL, pR, vL[3], vR[3];
     bool ok = primitives<DIM>(uL, gamma, rL, vL, pL, cL);
     ok = primitives<DIM>(uR, gamma, rR, vR, pR, cR) && ok;
@@ -149,9 +153,9 @@ __device__ __forceinline__ bool hllc(const Real *uL, const Real *uR, Real gamma,
     // region: 0 = left state, 1 = left star, 2 = right star, 3 = right state
     const int region = SL >= Real(0) ? 0 : (Ss >= Real(0) ? 1 : (SR >= Real(0) ? 2 : 3));
     const bool left = region <= 1;
-    Real uK[DIM + 2], vK[DIM];
+    Real uK[NC], vK[DIM];
 #pragma unroll
-    for (int f = 0; f < DIM + 2; ++f) uK[f] = left ? uL[f] : uR[f];
+    for (int f = 0; f < NC; ++f) uK[f] = left ? uL[f] : uR[f];
 #pragma unroll
     for (int b = 0; b < DIM; ++b) vK[b] = left ? vL[b] : vR[b];
     const Real rK = left ? rL : rR, pK = left ? pL : pR, vnK = left ? vnL : vnR;
@@ -164,31 +168,34 @@ __device__ __forceinline__ bool hllc(const Real *uL, const Real *uR, Real gamma,
 #pragma unroll
     for (int b = 0; b < DIM; ++b) F[1 + b] = uK[1 + b] * vnK + (b == a ? pK : Real(0));
     F[DIM + 1] = (uK[DIM + 1] + pK) * vnK;
+    if constexpr (TR) F[DIM + 2] = uK[DIM + 2] * vnK;
     if (region == 1 || region == 2) {
         const Real fac = rK * (SK - vnK) / (SK - Ss);
-        Real us[DIM + 2];
+        Real us[NC];
         us[0] = fac;
 #pragma unroll
         for (int b = 0; b < DIM; ++b) us[1 + b] = fac * (b == a ? Ss : vK[b]);
         us[DIM + 1] = fac * (uK[DIM + 1] / rK + (Ss - vnK) * (Ss + pK / (rK * (SK - vnK))));
+        if constexpr (TR) us[DIM + 2] = fac * (uK[DIM + 2] / rK);
 #pragma unroll
-        for (int f = 0; f < DIM + 2; ++f) F[f] += SK * (us[f] - uK[f]);
+        for (int f = 0; f < NC; ++f) F[f] += SK * (us[f] - uK[f]);
     }
     return ok;
 }
 
-template <int DIM, typename Real>
+template <int DIM, bool TR = false, typename Real>
 __device__ __forceinline__ bool hllc(const Real *uL, const Real *uR, Real gamma, int a, Real *F)
 {
     Real cL, cR;
-    return hllc<DIM>(uL, uR, gamma, a, F, cL, cR);
+    return hllc<DIM, TR>(uL, uR, gamma, a, F, cL, cR);
 }
 
 // Navier-Stokes flux along axis a (Sec. 3.3): (0, Pi_a, v.Pi_a + kappa (gamma-1) rho d_a u_int),
-// Pi = nu rho (grad v + grad v^T - 2/3 div v I).  grad[b][f] is the physical gradient.
-template <int DIM, typename Real>
-__device__ __forceinline__ void ns_flux(const Real *u, const Real (*grad)[DIM + 2], Real gamma, Real nu, Real kappa,
-                                        int a, Real *F)
+// Pi = nu rho (grad v + grad v^T - 2/3 div v I); TR: the tracer row eta rho d_a c =
+// eta (d_a (rho c) - c d_a rho) (Sec. 3.4).  grad[b][f] is the physical gradient.
+template <int DIM, bool TR = false, typename Real>
+__device__ __forceinline__ void ns_flux(const Real *u, const Real (*grad)[DIM + 2 + (TR ? 1 : 0)], Real gamma,
+                                        Real nu, Real kappa, Real eta, int a, Real *F)
 {
     const Real rho = u[0];
     const Real inv = Real(1) / rho;
@@ -215,6 +222,7 @@ __device__ __forceinline__ void ns_flux(const Real *u, const Real (*grad)[DIM + 
 #pragma unroll
     for (int c = 0; c < DIM; ++c) duint -= v[c] * dv[a][c];
     F[DIM + 1] = work + kappa * (gamma - Real(1)) * rho * duint;
+    if constexpr (TR) F[DIM + 2] = eta * (grad[a][DIM + 2] - u[DIM + 2] * inv * grad[a][0]);
 }
 
 // ------------------------------------------------------------------ shared memory plan

@@ -18,23 +18,23 @@
 namespace dgx {
 
 
-template <int DIM, int N, typename Real>
+template <int DIM, int N, typename Real, bool TR>
 struct LimiterPlan {
     static constexpr int Q = N + 1;
     static constexpr int E = Q + 2;  // Gauss points, then -1, then +1
     static constexpr int NP = DIM == 2 ? Q * Q : Q * Q * Q;
     static constexpr int NE = DIM == 2 ? E * E : E * E * E;
-    static constexpr int NC = DIM + 2;
+    static constexpr int NC = DIM + 2 + (TR ? 1 : 0);  // conserved fields (with a passive tracer)
     static constexpr size_t PER_CELL = sizeof(Real) * (size_t)NC * (NP + 2 * NE);
     static constexpr int CPB_RAW = (int)((96 * 1024) / PER_CELL);
     static constexpr int CPB = CPB_RAW >= 8 ? 8 : (CPB_RAW < 1 ? 1 : CPB_RAW);  // cells (= warps) per CTA
     static constexpr size_t BYTES = sizeof(Real) * (size_t)(E * Q) + PER_CELL * CPB;
 };
 
-template <int DIM, int N, typename Real>
+template <int DIM, int N, typename Real, bool TR>
 __global__ void limiter_kernel(const LimiterArgs A, const Tables<Real> Tg)
 {
-    using PL = LimiterPlan<DIM, N, Real>;
+    using PL = LimiterPlan<DIM, N, Real, TR>;
     constexpr int Q = PL::Q, E = PL::E, NP = PL::NP, NE = PL::NE, NC = PL::NC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Real *tE = reinterpret_cast<Real *>(smem_raw);  // [E][Q]: Pt_m at x_i, then at -1, +1
@@ -176,11 +176,11 @@ __global__ void limiter_kernel(const LimiterArgs A, const Tables<Real> Tg)
     }
 }
 
-template <int DIM, int N, typename Real>
+template <int DIM, int N, typename Real, bool TR>
 cudaError_t run_limiter(const LimiterArgs &a, const Tables<Real> &t, cudaStream_t s)
 {
-    using PL = LimiterPlan<DIM, N, Real>;
-    auto k = limiter_kernel<DIM, N, Real>;
+    using PL = LimiterPlan<DIM, N, Real, TR>;
+    auto k = limiter_kernel<DIM, N, Real, TR>;
     static bool attr_set = false;  // first call comes from the handle set-up
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::BYTES);
@@ -191,6 +191,12 @@ cudaError_t run_limiter(const LimiterArgs &a, const Tables<Real> &t, cudaStream_
     const long long blocks = (a.ncell + PL::CPB - 1) / PL::CPB;
     k<<<(unsigned)blocks, 32 * PL::CPB, PL::BYTES, s>>>(a, t);
     return cudaGetLastError();
+}
+
+template <int DIM, int N, typename Real>
+cudaError_t run_limiter_any(const LimiterArgs &a, const Tables<Real> &t, cudaStream_t s)
+{
+    return a.tracer_on ? run_limiter<DIM, N, Real, true>(a, t, s) : run_limiter<DIM, N, Real, false>(a, t, s);
 }
 
 }  // namespace dgx

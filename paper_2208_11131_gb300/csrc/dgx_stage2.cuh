@@ -38,16 +38,20 @@ __device__ __forceinline__ void cp_async_4(void *smem, const void *gmem)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-template <int DIM, int N, typename Real, bool AV, bool NS, int TX, int TY, int TZ, bool PF>
+template <int DIM, int N, typename Real, bool AV, int NSM, int TX, int TY, int TZ, bool PF>
 struct Stage2Plan {
     using S = Shape<DIM, N, TX, TY, TZ>;
+    // NSM: physical diffusive fluxes -- 0 none, 1 Navier-Stokes (Sec. 3.3), 2 Navier-Stokes with a
+    // passive tracer (Sec. 3.4, conserved field after the energy, whose diffusion needs the gradients)
+    static constexpr bool NS = NSM >= 1;
+    static constexpr bool TR = NSM == 2;
     // threads per CTA and the resident CTAs per SM the registers are bounded for (measured at
     // every degree): 2-D FP32 tiles balance their phases better over 10 warps (the 304 face
     // points of an 8x4 or 4x8 tile fit one round), 2 CTAs per SM; a 3-D FP32 tile fills most of
     // the shared memory, so one CTA per SM runs 16 warps to hide latency; FP64 uses 8 warps
     static constexpr int NTH = sizeof(Real) == 4 ? (DIM == 2 ? 320 : 512) : 256;
     static constexpr int MINB = (DIM == 2 && sizeof(Real) == 4) ? 2 : 1;
-    static constexpr int Q = S::Q, NP = S::NP, NPF = S::NPF, NC = S::NC;
+    static constexpr int Q = S::Q, NP = S::NP, NPF = S::NPF, NC = S::NC + (TR ? 1 : 0);
     static constexpr int NF = NC + (AV ? 1 : 0);
     static constexpr int TC = S::TC, NSLOT = S::NSLOT, NFACE = S::NFACE;
     static constexpr int TAB = (3 * Q * Q + 7 * Q + 1 + 3) / 4 * 4;
@@ -140,13 +144,14 @@ __device__ __forceinline__ void st_line(T *p, const T (&w)[Q])
 // Body shared by the single-simulation kernel (A0: its arguments) and the batched kernel (descs:
 // one argument set per simulation; tile_off: prefix sums of the simulations' tile counts, so the
 // work list is every (simulation, tile) pair in order).
-template <int DIM, int N, typename Real, bool AV, bool NS, int TX, int TY, int TZ, bool PF, bool BATCH>
+template <int DIM, int N, typename Real, bool AV, int NSM, int TX, int TY, int TZ, bool PF, bool BATCH>
 __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs *descs, const int *tile_off,
                                             int nsims, const Tables<Real> &Tg)
 {
     using S = Shape<DIM, N, TX, TY, TZ>;
-    using PL = Stage2Plan<DIM, N, Real, AV, NS, TX, TY, TZ, PF>;
-    constexpr int Q = S::Q, NP = S::NP, NPF = S::NPF, NC = S::NC, TC = S::TC, NSLOT = S::NSLOT;
+    using PL = Stage2Plan<DIM, N, Real, AV, NSM, TX, TY, TZ, PF>;
+    constexpr int Q = S::Q, NP = S::NP, NPF = S::NPF, NC = PL::NC, TC = S::TC, NSLOT = S::NSLOT;
+    constexpr bool NS = PL::NS, TR = PL::TR;
     constexpr int NF = PL::NF, NFACE = S::NFACE, NPS = PL::NPS, VEC = PL::VEC;
     constexpr bool GRAD = AV || NS;
 
@@ -318,7 +323,7 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
         const Real *K;
         if constexpr (sizeof(Real) == 4) K = A.kf;
         else K = A.kd;
-        const Real gamma = K[SK_GAMMA], nu = K[SK_NU], kappa = K[SK_KAPPA];
+        const Real gamma = K[SK_GAMMA], nu = K[SK_NU], kappa = K[SK_KAPPA], eta = K[SK_ETA];
         const Real epsfac = K[SK_EPS], inv_tau = K[SK_INV_TAU], f_v = K[SK_FV];
         const Real inv_f = Tg.inv_f;
         Real two_h[3], cax[3], inv_h[3];
@@ -501,10 +506,10 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
 #pragma unroll
                 for (int a = 0; a < DIM; ++a) {
                     Real F[NC];
-                    euler_flux<DIM>(u, v, p, a, F);
+                    euler_flux<DIM, TR>(u, v, p, a, F);
                     if (NS) {
                         Real Fn[NC];
-                        ns_flux<DIM>(u, gr, gamma, nu, kappa, a, Fn);
+                        ns_flux<DIM, TR>(u, gr, gamma, nu, kappa, eta, a, Fn);
 #pragma unroll
                         for (int f = 0; f < NC; ++f) F[f] -= Fn[f];
                     }
@@ -622,7 +627,7 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                     u[f] = acc;
                 }
                 if (!primitives<DIM>(u, gamma, rho, v, pr_, cs)) bad = 1;
-                euler_flux<DIM>(u, v, pr_, a, Fh);
+                euler_flux<DIM, TR>(u, v, pr_, a, Fh);
             } else {
                 Real uL[NC + 1], uR[NC + 1];
 #pragma unroll
@@ -639,7 +644,7 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                     uR[f] = ar;
                 }
                 Real cL, cR;  // trace sound speeds, reused by the artificial viscosity below
-                if (!hllc<DIM>(uL, uR, gamma, a, Fh, cL, cR)) bad = 1;
+                if (!hllc<DIM, TR>(uL, uR, gamma, a, Fh, cL, cR)) bad = 1;
                 if (GRAD) {
                     Real dn[NC];
                     const Real sc = inv_f * inv_h[a];
@@ -678,7 +683,7 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                         }
                         if (!(ut[0] > Real(0))) bad = 1;
                         Real Fn[NC];
-                        ns_flux<DIM>(ut, grd, gamma, nu, kappa, a, Fn);
+                        ns_flux<DIM, TR>(ut, grd, gamma, nu, kappa, eta, a, Fn);
 #pragma unroll
                         for (int f = 0; f < NC; ++f) Fh[f] -= Fn[f];
                     }
@@ -723,7 +728,7 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                 r = fma(-tLp[i], sFh[(f * NFACE + fl + 1) * NPF + k], r);
             }
             const int ri = fc * NPS + n;
-            if (A.force && f > 0) r += sR[ri];
+            if (A.force && f > 0 && f <= DIM + 1) r += sR[ri];  // momentum and energy
             sR[ri] = r;
         }
         __syncthreads();
@@ -882,29 +887,29 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
     }
 }
 
-template <int DIM, int N, typename Real, bool AV, bool NS, int TX, int TY, int TZ, bool PF>
-__global__ void __launch_bounds__(Stage2Plan<DIM, N, Real, AV, NS, TX, TY, TZ, PF>::NTH,
-                                  Stage2Plan<DIM, N, Real, AV, NS, TX, TY, TZ, PF>::MINB)
+template <int DIM, int N, typename Real, bool AV, int NSM, int TX, int TY, int TZ, bool PF>
+__global__ void __launch_bounds__(Stage2Plan<DIM, N, Real, AV, NSM, TX, TY, TZ, PF>::NTH,
+                                  Stage2Plan<DIM, N, Real, AV, NSM, TX, TY, TZ, PF>::MINB)
     stage2_kernel(const StageArgs A, const Tables<Real> Tg)
 {
-    stage2_body<DIM, N, Real, AV, NS, TX, TY, TZ, PF, false>(&A, nullptr, nullptr, 1, Tg);
+    stage2_body<DIM, N, Real, AV, NSM, TX, TY, TZ, PF, false>(&A, nullptr, nullptr, 1, Tg);
 }
 
-template <int DIM, int N, typename Real, bool AV, bool NS, int TX, int TY, int TZ, bool PF>
-__global__ void __launch_bounds__(Stage2Plan<DIM, N, Real, AV, NS, TX, TY, TZ, PF>::NTH,
-                                  Stage2Plan<DIM, N, Real, AV, NS, TX, TY, TZ, PF>::MINB)
+template <int DIM, int N, typename Real, bool AV, int NSM, int TX, int TY, int TZ, bool PF>
+__global__ void __launch_bounds__(Stage2Plan<DIM, N, Real, AV, NSM, TX, TY, TZ, PF>::NTH,
+                                  Stage2Plan<DIM, N, Real, AV, NSM, TX, TY, TZ, PF>::MINB)
     stage2_batch_kernel(const StageArgs *descs, const int *tile_off, int nsims, const Tables<Real> Tg)
 {
-    stage2_body<DIM, N, Real, AV, NS, TX, TY, TZ, PF, true>(nullptr, descs, tile_off, nsims, Tg);
+    stage2_body<DIM, N, Real, AV, NSM, TX, TY, TZ, PF, true>(nullptr, descs, tile_off, nsims, Tg);
 }
 
-template <int DIM, int N, typename Real, bool AV, bool NS, int TX, int TY, int TZ>
+template <int DIM, int N, typename Real, bool AV, int NSM, int TX, int TY, int TZ>
 cudaError_t run_stage2(const StageArgs &a, const Tables<Real> &t, cudaStream_t s, int *grid_out)
 {
     // prefetch buffers when the tile still fits in shared memory with them
-    constexpr bool PF = Stage2Plan<DIM, N, Real, AV, NS, TX, TY, TZ, true>::BYTES <= 227 * 1024;
-    using PL = Stage2Plan<DIM, N, Real, AV, NS, TX, TY, TZ, PF>;
-    auto k = stage2_kernel<DIM, N, Real, AV, NS, TX, TY, TZ, PF>;
+    constexpr bool PF = Stage2Plan<DIM, N, Real, AV, NSM, TX, TY, TZ, true>::BYTES <= 227 * 1024;
+    using PL = Stage2Plan<DIM, N, Real, AV, NSM, TX, TY, TZ, PF>;
+    auto k = stage2_kernel<DIM, N, Real, AV, NSM, TX, TY, TZ, PF>;
     static_assert(PL::BYTES <= 227 * 1024, "stage2 tile exceeds shared memory");
     static int blocks_per_sm = 0;
     static int sms = 0;
@@ -929,13 +934,13 @@ cudaError_t run_stage2(const StageArgs &a, const Tables<Real> &t, cudaStream_t s
 }
 
 // batched launch: one persistent grid over the (simulation, tile) work list of a group
-template <int DIM, int N, typename Real, bool AV, bool NS, int TX, int TY, int TZ>
+template <int DIM, int N, typename Real, bool AV, int NSM, int TX, int TY, int TZ>
 cudaError_t run_stage2_batch(const StageArgs *descs, const int *tile_off, int nsims, int total_tiles,
                              const Tables<Real> &t, cudaStream_t s)
 {
-    constexpr bool PF = Stage2Plan<DIM, N, Real, AV, NS, TX, TY, TZ, true>::BYTES <= 227 * 1024;
-    using PL = Stage2Plan<DIM, N, Real, AV, NS, TX, TY, TZ, PF>;
-    auto k = stage2_batch_kernel<DIM, N, Real, AV, NS, TX, TY, TZ, PF>;
+    constexpr bool PF = Stage2Plan<DIM, N, Real, AV, NSM, TX, TY, TZ, true>::BYTES <= 227 * 1024;
+    using PL = Stage2Plan<DIM, N, Real, AV, NSM, TX, TY, TZ, PF>;
+    auto k = stage2_batch_kernel<DIM, N, Real, AV, NSM, TX, TY, TZ, PF>;
     static int blocks_per_sm = 0;
     static int sms = 0;
     if (!blocks_per_sm) {  // first call comes from the batch set-up, never from a graph capture
@@ -961,23 +966,27 @@ cudaError_t run_stage2_batch_any(int av, int ns, const StageArgs *descs, const i
                                  int total_tiles, const Tables<Real> &t, cudaStream_t s)
 {
     if (av) {
-        if (ns) return run_stage2_batch<DIM, N, Real, true, true, TX, TY, TZ>(descs, tile_off, nsims, total_tiles, t, s);
-        return run_stage2_batch<DIM, N, Real, true, false, TX, TY, TZ>(descs, tile_off, nsims, total_tiles, t, s);
+        if (ns) return run_stage2_batch<DIM, N, Real, true, 1, TX, TY, TZ>(descs, tile_off, nsims, total_tiles, t, s);
+        return run_stage2_batch<DIM, N, Real, true, 0, TX, TY, TZ>(descs, tile_off, nsims, total_tiles, t, s);
     }
-    if (ns) return run_stage2_batch<DIM, N, Real, false, true, TX, TY, TZ>(descs, tile_off, nsims, total_tiles, t, s);
-    return run_stage2_batch<DIM, N, Real, false, false, TX, TY, TZ>(descs, tile_off, nsims, total_tiles, t, s);
+    if (ns) return run_stage2_batch<DIM, N, Real, false, 1, TX, TY, TZ>(descs, tile_off, nsims, total_tiles, t, s);
+    return run_stage2_batch<DIM, N, Real, false, 0, TX, TY, TZ>(descs, tile_off, nsims, total_tiles, t, s);
 }
 
-// run-time (AV, NS) dispatch onto the compile-time variants
+// run-time (AV, diffusion mode) dispatch onto the compile-time variants; a tracer always takes the
+// diffusive path (its eta, nu and kappa may be zero)
 template <int DIM, int N, typename Real, int TX, int TY, int TZ>
 cudaError_t run_stage2_any(const StageArgs &a, const Tables<Real> &t, cudaStream_t s, int *grid)
 {
+    const int m = a.tracer_on ? 2 : (a.ns_on ? 1 : 0);
     if (a.av_on) {
-        if (a.ns_on) return run_stage2<DIM, N, Real, true, true, TX, TY, TZ>(a, t, s, grid);
-        return run_stage2<DIM, N, Real, true, false, TX, TY, TZ>(a, t, s, grid);
+        if (m == 2) return run_stage2<DIM, N, Real, true, 2, TX, TY, TZ>(a, t, s, grid);
+        if (m == 1) return run_stage2<DIM, N, Real, true, 1, TX, TY, TZ>(a, t, s, grid);
+        return run_stage2<DIM, N, Real, true, 0, TX, TY, TZ>(a, t, s, grid);
     }
-    if (a.ns_on) return run_stage2<DIM, N, Real, false, true, TX, TY, TZ>(a, t, s, grid);
-    return run_stage2<DIM, N, Real, false, false, TX, TY, TZ>(a, t, s, grid);
+    if (m == 2) return run_stage2<DIM, N, Real, false, 2, TX, TY, TZ>(a, t, s, grid);
+    if (m == 1) return run_stage2<DIM, N, Real, false, 1, TX, TY, TZ>(a, t, s, grid);
+    return run_stage2<DIM, N, Real, false, 0, TX, TY, TZ>(a, t, s, grid);
 }
 
 }  // namespace dgx

@@ -43,7 +43,8 @@ class dg_params(ctypes.Structure):
                 ("av_on", ctypes.c_int), ("av_scale", ctypes.c_double), ("f_v", ctypes.c_double),
                 ("f_tau", ctypes.c_double), ("f_w", ctypes.c_double), ("s_onset", ctypes.c_double),
                 ("positivity_on", ctypes.c_int), ("forcing_on", ctypes.c_int), ("force_amp", ctypes.c_double),
-                ("force_ts", ctypes.c_double), ("force_dt", ctypes.c_double), ("force_seed", ctypes.c_ulonglong)]
+                ("force_ts", ctypes.c_double), ("force_dt", ctypes.c_double), ("force_seed", ctypes.c_ulonglong),
+                ("tracer_on", ctypes.c_int), ("tracer_eta", ctypes.c_double)]
 
 FORCING_STATE = 97  # DG_FORCING_STATE
 
@@ -292,13 +293,16 @@ class Simulation:
         p.cfl = wl.cfl if cfl is None else cfl
         p.av_on = int(wl.av_on)
         p.positivity_on = int(getattr(wl, "positivity_on", 0))
+        if getattr(wl, "tracer_on", 0):
+            p.tracer_on = 1
+            p.tracer_eta = float(wl.eta)
         if getattr(wl, "forcing_on", 0):
             p.forcing_on = 1
             p.force_amp, p.force_ts, p.force_dt = wl.force_amp, wl.force_ts, wl.force_dt
             p.force_seed = int(wl.force_seed) & 0xFFFFFFFFFFFFFFFF
         dg_set_params(self.h, p)
         self.nf, self.M, self.ncell = dg_sizes(self.h)
-        self.nc = wl.dim + 2
+        self.nc = wl.dim + 2 + (1 if getattr(wl, "tracer_on", 0) else 0)
 
     def close(self):
         if self.h:

@@ -34,6 +34,7 @@ def rhs_scale(prob, w, ref):
     term is of that size, and rounding errors scale with it, not with the possibly cancelled result):
     lambda = max c_s + max |v| over the Gauss points, then over h_min
       rho: max rho lambda;  momentum: max rho lambda^2 (covers rho v^2 and p);  energy: gamma max e lambda;
+      tracer rho c: max rho c lambda;
       alpha: (1 + max|alpha|) lambda (source terms f_v |div v| and alpha P c_s / (f_tau h))."""
     cm, vm, _ = oracle.max_speeds(prob, w)
     lam = cm + vm
@@ -41,8 +42,12 @@ def rhs_scale(prob, w, ref):
     d = prob.dim
     rho = np.abs(w[0, :, 0]).max()
     sc = [rho * lam / h] + [rho * lam * lam / h] * d + [prob.gamma * np.abs(w[d + 1, :, 0]).max() * lam / h]
-    if ref.shape[0] > d + 2:
-        sc.append((1.0 + np.abs(w[d + 2, :, 0]).max()) * lam / h)
+    nc = d + 2
+    if getattr(prob, "tracer_on", 0):  # tracer rho c: flux c rho v, like the density
+        sc.append(max(np.abs(w[d + 2, :, 0]).max(), 1e-300) * lam / h)
+        nc += 1
+    if ref.shape[0] > nc:
+        sc.append((1.0 + np.abs(w[nc, :, 0]).max()) * lam / h)
     return np.maximum(np.array(sc), np.abs(ref).reshape(ref.shape[0], -1).max(1))
 
 
@@ -59,7 +64,11 @@ def state_scale(prob, ref):
     d = prob.dim
     rho = np.abs(ref[0]).max()
     sc = [rho] + [rho * (cm + vm)] * d + [np.abs(ref[d + 1]).max()]
-    if ref.shape[0] > d + 2:
+    nc = d + 2
+    if getattr(prob, "tracer_on", 0):
+        sc.append(rho)  # rho c with c of order one
+        nc += 1
+    if ref.shape[0] > nc:
         sc.append(1.0)
     return np.array(sc)
 
