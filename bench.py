@@ -178,6 +178,28 @@ def allreduce_max(x, ws):
     return float(t.item())
 
 
+def l1_error_of(wl, w, func):
+    """L1 density error against a closed form with the n+2 point rule of the error norm (Sec. 5.1)"""
+    import numpy as np
+    from numpy.polynomial import legendre as L
+    q = wl.n + 2
+    x, g = L.leggauss(q)
+    d = wl.dim
+    idx = np.stack(np.meshgrid(*([np.arange(q)] * d), indexing="ij")[::-1], -1).reshape(-1, d)
+    xi, G = x[idx], np.prod(g[idx], 1)
+    midx = np.stack(np.meshgrid(*([np.arange(wl.n + 1)] * d), indexing="ij")[::-1], -1).reshape(-1, d)
+    phi = np.ones((len(xi), len(midx)))
+    for a in range(d):
+        Pt = np.stack([np.sqrt(2 * l + 1) * L.legval(xi[:, a], [0] * l + [1]) for l in range(wl.n + 1)], 1)
+        phi *= Pt[:, midx[:, a]]
+    axes = [wl.lo[a] + (np.arange(wl.N[a]) + 0.5) * wl.h[a] for a in range(d)]
+    xc = np.stack([m.reshape(-1) for m in np.meshgrid(*axes[::-1], indexing="ij")[::-1]], 1)
+    X = (xc[:, None, :] + 0.5 * np.array(wl.h[:d]) * xi[None]).reshape(-1, d)
+    ex = np.asarray(func(X))[0].reshape(wl.ncell, len(xi))
+    num = w[0] @ phi.T
+    return float(np.sum(np.abs(ex - num) * G[None, :]) / 2.0 ** d / wl.ncell)
+
+
 def oracle_problem(wl):
     import oracle
     return oracle.Problem(dim=wl.dim, n=wl.n, N=tuple(wl.N[:wl.dim]), lo=tuple(wl.lo[:wl.dim]),
@@ -276,6 +298,57 @@ def ensemble_measurement(dgx, inputs, torch, stream, steps: int, warmup: int):
             "one_by_one": {"ms_per_step": ms_s, "value": units / (ms_s / 1e3), "unit": UNIT},
             "speedup": ms_s / ms_b,
             "l2": "not flushed; the members' state alone exceeds L2"}
+
+
+def side_workloads(dgx, inputs, oracle_l1, torch, stream, flush):
+    """throughput of the other paths at their own sizes (FP32-bulk, L2 flushed before each timed
+    step): the shear layer with a passive dye (Sec. 3.4), the 128^3 driven turbulence box (Sec. 6,
+    3-D, working set above L2), and the metric's same-L1-error check on the 32^2 density wave."""
+    import numpy as np
+    out = {}
+
+    def timed(wl, w0, steps, warm, stages):
+        sim = dgx.Simulation(wl, precision=dgx.DG_FP32_BULK)
+        sim.set_stream(stream)
+        sim.set_state(w0)
+        for _ in range(warm):
+            dgx.dg_step_timed(sim.h, 0.0, 7)
+        ms = []
+        for k in range(steps):
+            flush.fill_(k & 0xFF)
+            ms.append(sum(dgx.dg_step_timed(sim.h, 0.0, 7)))
+        sim.close()
+        m = float(np.mean(ms))
+        return {"ms_per_step": m, "value": wl.dofs * stages / (m / 1e3), "unit": UNIT, "steps": steps}
+
+    wl = inputs.c2_shear_layer(N=256, n=3).with_(tracer_on=1, eta=1e-5)
+    w = inputs.project(wl.with_(tracer_on=0), inputs.shear_layer_ic(wl.with_(tracer_on=0)))
+    # dye: concentration 1 in the lower-density layer (|y - 1| > 0.5) and 0 elsewhere, smoothed
+    c = inputs.project(wl.with_(tracer_on=0, av_on=0), lambda X: np.stack(
+        [0.5 * (np.tanh((np.abs(X[:, 1] - 1.0) - 0.5) / 0.05) + 1.0)] * 4))[0]
+    rc = np.zeros_like(c)
+    rc[:, 0] = w[0, :, 0] * c[:, 0]  # rho c from the cell means (a dye of the layers)
+    w0 = np.ascontiguousarray(np.concatenate([w[:4], rc[None], w[4:]]))
+    out["tracer"] = dict(timed(wl, w0, 10, 3, 5), workload="ns_shear_layer_2d_256x256_deg3_av_with_dye")
+
+    wl = inputs.c4_turbulence_box(N=128, n=3)
+    out["turbulence_box"] = dict(timed(wl, inputs.rest_state(wl), 4, 2, 5),
+                                 workload="driven_turbulence_3d_128cubed_deg3_av_ns_forcing")
+
+    wl = inputs.c1_density_wave(N=32, n=2)
+    w0 = inputs.project(wl, inputs.density_wave_ic(wl, 0.0))
+    errs = {}
+    for name, prec in (("fp64", dgx.DG_FP64), ("fp32", dgx.DG_FP32_BULK)):
+        sim = dgx.Simulation(wl, precision=prec)
+        sim.set_state(w0)
+        for _ in range(20):
+            sim.step()
+        T = sim.get_aux()[2][2]
+        errs[name] = oracle_l1(wl, sim.get_state(), inputs.density_wave_ic(wl, T))
+        sim.close()
+    out["same_l1_c1"] = {"workload": "density_wave_2d_32x32_deg2_20_steps", "l1_rho_fp64": errs["fp64"],
+                         "l1_rho_fp32": errs["fp32"], "rel_diff": abs(errs["fp32"] / errs["fp64"] - 1)}
+    return out
 
 
 def dgx_arm(args, rank, ws, local):
@@ -396,6 +469,8 @@ def dgx_arm(args, rank, ws, local):
     sim.close()
     if not args.no_ensemble:
         line["ensemble"] = ensemble_measurement(dgx, inputs, torch, stream, steps=20, warmup=3)
+    if not args.no_extras and rank == 0:
+        line["other_paths"] = side_workloads(dgx, inputs, l1_error_of, torch, stream, flush)
     if rank == 0:
         print(json.dumps(line), flush=True)
 

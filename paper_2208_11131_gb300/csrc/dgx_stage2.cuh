@@ -904,10 +904,21 @@ __global__ void __launch_bounds__(Stage2Plan<DIM, N, Real, AV, NSM, TX, TY, TZ, 
 }
 
 template <int DIM, int N, typename Real, bool AV, int NSM, int TX, int TY, int TZ>
+constexpr bool stage2_prefetch()
+{
+    using P1 = Stage2Plan<DIM, N, Real, AV, NSM, TX, TY, TZ, true>;
+    using P0 = Stage2Plan<DIM, N, Real, AV, NSM, TX, TY, TZ, false>;
+    constexpr size_t sm = 228 * 1024, reserve = 1024;  // shared memory per SM, reserved per CTA
+    if (P1::BYTES > 227 * 1024) return false;
+    return P1::MINB * (P1::BYTES + reserve) <= sm || P0::MINB * (P0::BYTES + reserve) > sm;
+}
+
+template <int DIM, int N, typename Real, bool AV, int NSM, int TX, int TY, int TZ>
 cudaError_t run_stage2(const StageArgs &a, const Tables<Real> &t, cudaStream_t s, int *grid_out)
 {
-    // prefetch buffers when the tile still fits in shared memory with them
-    constexpr bool PF = Stage2Plan<DIM, N, Real, AV, NSM, TX, TY, TZ, true>::BYTES <= 227 * 1024;
+    // prefetch buffers when the tile still fits in shared memory with them, as many times per SM
+    // as the registers are bounded for (else the resident CTAs, not the prefetch, hide latency)
+    constexpr bool PF = stage2_prefetch<DIM, N, Real, AV, NSM, TX, TY, TZ>();
     using PL = Stage2Plan<DIM, N, Real, AV, NSM, TX, TY, TZ, PF>;
     auto k = stage2_kernel<DIM, N, Real, AV, NSM, TX, TY, TZ, PF>;
     static_assert(PL::BYTES <= 227 * 1024, "stage2 tile exceeds shared memory");
@@ -938,7 +949,7 @@ template <int DIM, int N, typename Real, bool AV, int NSM, int TX, int TY, int T
 cudaError_t run_stage2_batch(const StageArgs *descs, const int *tile_off, int nsims, int total_tiles,
                              const Tables<Real> &t, cudaStream_t s)
 {
-    constexpr bool PF = Stage2Plan<DIM, N, Real, AV, NSM, TX, TY, TZ, true>::BYTES <= 227 * 1024;
+    constexpr bool PF = stage2_prefetch<DIM, N, Real, AV, NSM, TX, TY, TZ>();
     using PL = Stage2Plan<DIM, N, Real, AV, NSM, TX, TY, TZ, PF>;
     auto k = stage2_batch_kernel<DIM, N, Real, AV, NSM, TX, TY, TZ, PF>;
     static int blocks_per_sm = 0;
