@@ -56,7 +56,7 @@ class Cfg(ctypes.Structure):
         ("positivity_on", ctypes.c_int), ("cfl", ctypes.c_double), ("rk_stages", ctypes.c_int),
         ("forcing_on", ctypes.c_int), ("force_amp", ctypes.c_double), ("force_ts", ctypes.c_double),
         ("force_dt", ctypes.c_double), ("force_seed", ctypes.c_ulonglong),
-        ("tracer_on", ctypes.c_int), ("eta", ctypes.c_double),
+        ("tracer_on", ctypes.c_int), ("eta", ctypes.c_double), ("basis", ctypes.c_int),
     ]
 
 FMODES = 16  # forcing-state mode stride
@@ -90,6 +90,7 @@ def lib():
             "or_forcing_normal": (D, [ctypes.c_ulonglong, ctypes.c_ulonglong]),
             "or_forcing_update": (I, [C, P, D]), "or_forcing_eval": (I, [C, P, I, P, P]),
             "or_hllc_tracer": (I, [I, I, D, P, P, P]),
+            "or_num_modes": (I, [I, I, I]), "or_basis_eval_b": (I, [I, I, I, I, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -162,11 +163,12 @@ def rk_stages(n: int) -> int:
     return lib().or_rk_stages(n)
 
 
-def basis_eval(dim: int, n: int, xi: np.ndarray) -> np.ndarray:
+def basis_eval(dim: int, n: int, xi: np.ndarray, basis: int = 0) -> np.ndarray:
+    """phi_l at reference points xi [npts, dim] -> [npts, M]; basis 1: the total-degree modes"""
     xi = np.ascontiguousarray(xi, dtype=np.float64).reshape(-1, dim)
-    M = (n + 1) ** dim
+    M = lib().or_num_modes(dim, n, basis)
     out = np.zeros((xi.shape[0], M))
-    lib().or_basis_eval(dim, n, xi.shape[0], _p(xi), _p(out))
+    lib().or_basis_eval_b(dim, n, basis, xi.shape[0], _p(xi), _p(out))
     return out
 
 
@@ -208,6 +210,7 @@ class Problem:
     force_seed: int = 0
     tracer_on: int = 0
     eta: float = 0.0
+    basis: int = 0  # 0 tensor product, 1 total degree l_x + l_y + l_z <= n (Sec. 2.3)
 
     def cfg(self) -> Cfg:
         c = Cfg()
@@ -226,6 +229,7 @@ class Problem:
                                                              self.force_dt)
         c.force_seed = int(self.force_seed) & 0xFFFFFFFFFFFFFFFF
         c.tracer_on, c.eta = int(self.tracer_on), float(self.eta)
+        c.basis = int(self.basis)
         return c
 
     @property
@@ -234,7 +238,7 @@ class Problem:
 
     @property
     def M(self) -> int:
-        return (self.n + 1) ** self.dim
+        return lib().or_num_modes(self.dim, self.n, int(self.basis))
 
     @property
     def nfields(self) -> int:
@@ -270,7 +274,7 @@ def project(prob: Problem, func, q: int | None = None) -> np.ndarray:
     """
     q = prob.n + 3 if q is None else q
     xi, G = _ref_points(prob.dim, q)
-    phi = basis_eval(prob.dim, prob.n, xi)  # [nq, M]
+    phi = basis_eval(prob.dim, prob.n, xi, prob.basis)  # [nq, M]
     xc = prob.cell_centres()
     h = np.array(prob.h)
     X = xc[:, None, :] + 0.5 * h[None, None, :] * xi[None, :, :]  # [ncell, nq, dim]
@@ -282,7 +286,7 @@ def project(prob: Problem, func, q: int | None = None) -> np.ndarray:
 
 def evaluate(prob: Problem, w: np.ndarray, xi: np.ndarray) -> np.ndarray:
     """values of every field at reference points xi [npts, dim] of every cell -> [nf, ncell, npts]."""
-    phi = basis_eval(prob.dim, prob.n, xi)
+    phi = basis_eval(prob.dim, prob.n, xi, prob.basis)
     return np.einsum("fkl,jl->fkj", w, phi)
 
 

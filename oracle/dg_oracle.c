@@ -89,6 +89,9 @@ typedef struct {
     /* passive tracer (Sec. 3.4): conserved field rho c after the energy, diffusivity eta */
     int tracer_on;
     double eta;
+    /* basis (Sec. 2.3): 0 full tensor product (every l_a <= n), 1 the paper's total-degree set
+     * (l_x + l_y + l_z <= n) */
+    int basis;
 } or_cfg;
 
 /* ------------------------------------------------------------------ */
@@ -192,6 +195,36 @@ static int flat(const int *idx, int base, int d)
     return r;
 }
 
+#define OR_MAXM (OR_MAXQ * OR_MAXQ * OR_MAXQ)
+
+/* modes of the basis (Sec. 2.3): products Pt_lx Pt_ly Pt_lz with every l_a <= n (basis 0) or with
+ * l_x + l_y + l_z <= n (basis 1, the paper's truncation), in tensor order (x fastest);
+ * exps[l] = (l_x, l_y, l_z), mode_of[tensor index] = l or -1 if absent; returns the count */
+static int mode_list(int d, int n, int basis, int (*exps)[3], int *mode_of)
+{
+    int Q = n + 1, T = 1, M = 0;
+    for (int a = 0; a < d; ++a) T *= Q;
+    for (int t = 0; t < T; ++t) {
+        int ll[3] = {0, 0, 0};
+        unflat(t, Q, d, ll);
+        int sum = ll[0] + ll[1] + ll[2];
+        if (basis == 1 && sum > n) {
+            mode_of[t] = -1;
+            continue;
+        }
+        for (int a = 0; a < 3; ++a) exps[M][a] = ll[a];
+        mode_of[t] = M++;
+    }
+    return M;
+}
+
+int or_num_modes(int d, int n, int basis)
+{
+    int exps[OR_MAXM][3], mode_of[OR_MAXM];
+    if (d < 2 || d > 3 || n < 0 || n > OR_MAXN) return -1;
+    return mode_list(d, n, basis, exps, mode_of);
+}
+
 /* the transverse axes of a face normal to `ax`, in increasing order */
 static void transverse_axes(int d, int ax, int *ta)
 {
@@ -224,16 +257,16 @@ int or_recovery_matrices(int n, double f, double *Am, double *Ap)
 
 double or_overlap_fraction(int n) { return n <= 2 ? 0.75 : 1.0; }
 
-static int tab_init(or_tab *T, int d, int n)
+static int tab_init(or_tab *T, int d, int n, int M_, const int (*exps)[3])
 {
     int Q = n + 1;
     T->d = d;
     T->n = n;
     T->Q = Q;
-    T->M = 1;
-    for (int a = 0; a < d; ++a) T->M *= Q;
-    T->NQ = T->M;
-    T->NQF = T->M / Q;
+    T->M = M_;
+    T->NQ = 1;
+    for (int a = 0; a < d; ++a) T->NQ *= Q;
+    T->NQF = T->NQ / Q;
     T->MT = T->NQF;
     or_gauss(Q, T->xg, T->wg);
     int M = T->M, NQ = T->NQ, NQF = T->NQF, MT = T->MT;
@@ -253,8 +286,7 @@ static int tab_init(or_tab *T, int d, int n)
         for (int a = 0; a < d; ++a) g *= T->wg[jj[a]];
         T->G[j] = g;
         for (int l = 0; l < M; ++l) {
-            int ll[3];
-            unflat(l, Q, d, ll);
+            const int *ll = exps[l];
             double v = 1.0;
             for (int a = 0; a < d; ++a) v *= or_pt(ll[a], T->xg[jj[a]]);
             T->phi[j * M + l] = v;
@@ -284,8 +316,7 @@ static int tab_init(or_tab *T, int d, int n)
                 xi[ax] = s ? 1.0 : -1.0;
                 for (int a = 0; a < d - 1; ++a) xi[ta[a]] = T->xg[kk[a]];
                 for (int l = 0; l < M; ++l) {
-                    int ll[3];
-                    unflat(l, Q, d, ll);
+                    const int *ll = exps[l];
                     double v = 1.0;
                     for (int a = 0; a < d; ++a) v *= or_pt(ll[a], xi[a]);
                     T->phif[((ax * 2 + s) * NQF + k) * M + l] = v;
@@ -380,10 +411,6 @@ static void euler_flux_tr(const double *u, const or_prim *P, int d, int tr, int 
     if (tr) F[d + 2] = u[d + 2] * vn;
 }
 
-static void euler_flux(const double *u, const or_prim *P, int d, int ax, double *F)
-{
-    euler_flux_tr(u, P, d, 0, ax, F);
-}
 
 /* HLLC flux along axis ax (Toro), Davis wave-speed estimates; a passive tracer (tr = 1) is carried
  * in the star states with the concentration of its side, c_K rho*_K */
@@ -490,6 +517,9 @@ typedef struct {
     int P;
     int need_grad;
     int diss; /* physical diffusive fluxes: NS (nu, kappa) and/or tracer diffusion (eta) */
+    int basis;
+    int exps[OR_MAXM][3]; /* exponents of mode l */
+    int mode_of[OR_MAXM]; /* mode of a tensor index, -1 if not in the basis */
 } or_geo;
 
 static void geo_init(or_geo *g, const or_cfg *c)
@@ -497,12 +527,11 @@ static void geo_init(or_geo *g, const or_cfg *c)
     g->d = c->dim;
     g->n = c->n;
     g->Q = c->n + 1;
-    g->M = 1;
+    g->basis = c->basis;
     g->ncell = 1;
     for (int a = 0; a < 3; ++a) g->N[a] = 1;
     g->hmin = 1e300;
     for (int a = 0; a < c->dim; ++a) {
-        g->M *= g->Q;
         g->N[a] = c->N[a];
         g->ncell *= c->N[a];
         g->h[a] = (c->hi[a] - c->lo[a]) / c->N[a];
@@ -515,6 +544,7 @@ static void geo_init(or_geo *g, const or_cfg *c)
     g->P = c->n + 1;
     g->diss = c->nu > 0.0 || c->kappa > 0.0 || (g->TR && c->eta > 0.0);
     g->need_grad = c->av_on || g->diss;
+    g->M = mode_list(c->dim, c->n, c->basis, g->exps, g->mode_of);
 }
 
 static long cell_index(const or_geo *g, const int *ci)
@@ -544,6 +574,7 @@ static int check_cfg(const or_cfg *c)
     if (c->forcing_on && (!(c->force_ts > 0.0) || !(c->force_dt > 0.0) || !(c->force_amp >= 0.0)))
         return OR_EINVAL;
     if (c->tracer_on && !(c->eta >= 0.0)) return OR_EINVAL;
+    if (c->basis != 0 && c->basis != 1) return OR_EINVAL;
     return OR_OK;
 }
 
@@ -713,7 +744,8 @@ static void face_recovery(const or_tab *T, const or_geo *g, const double *w, lon
                     int ll[3];
                     ll[ax] = m;
                     for (int a = 0; a < d - 1; ++a) ll[ta[a]] = tt[a];
-                    int l = flat(ll, Q, d);
+                    int l = g->mode_of[flat(ll, Q, d)];
+                    if (l < 0) continue; /* absent from the basis: zero weight */
                     acc += T->Am[m][la] * W(w, g, f, KL, l) + T->Ap[m][la] * W(w, g, f, KR, l);
                 }
                 q[la][t] = 0.5 * acc;
@@ -819,7 +851,7 @@ int or_rhs_forced(const or_cfg *c, const double *w, const double *wig, const dou
     or_geo g;
     geo_init(&g, c);
     or_tab T;
-    if (tab_init(&T, g.d, g.n)) return OR_EINVAL;
+    if (tab_init(&T, g.d, g.n, g.M, (const int(*)[3])g.exps)) return OR_EINVAL;
     int d = g.d, M = g.M, NQ = T.NQ, NQF = T.NQF, NF = g.NF, FT = g.FT;
     int status = OR_OK;
     double two1d = ldexp(1.0, 1 - d), two_d = ldexp(1.0, -d);
@@ -965,7 +997,7 @@ int or_max_speeds(const or_cfg *c, const double *w, double *cmax, double *vmax)
     or_geo g;
     geo_init(&g, c);
     or_tab T;
-    if (tab_init(&T, g.d, g.n)) return OR_EINVAL;
+    if (tab_init(&T, g.d, g.n, g.M, (const int(*)[3])g.exps)) return OR_EINVAL;
     double cm = 0.0, vm = 0.0;
     int status = OR_OK;
 #pragma omp parallel for schedule(static) reduction(max : cm, vm) reduction(| : status)
@@ -1010,11 +1042,15 @@ int or_sensor(const or_cfg *c, const double *w, double *S)
     for (long K = 0; K < g.ncell; ++K) {
         double hi = 0.0, all = 0.0;
         for (int l = 0; l < g.M; ++l) {
-            int ll[3];
-            unflat(l, g.Q, g.d, ll);
+            const int *ll = g.exps[l];
+            /* the modes the degree-(n-1) basis lacks: some l_a = n (tensor), l_x+l_y+l_z = n (total) */
             int top = 0;
-            for (int a = 0; a < g.d; ++a)
-                if (ll[a] == g.n) top = 1;
+            if (g.basis == 1) {
+                top = ll[0] + ll[1] + ll[2] == g.n;
+            } else {
+                for (int a = 0; a < g.d; ++a)
+                    if (ll[a] == g.n) top = 1;
+            }
             double v = W(w, &g, 0, K, l);
             all += v * v;
             if (top && g.n > 0) hi += v * v;
@@ -1055,7 +1091,7 @@ int or_positivity(const or_cfg *c, double *w)
     or_geo g;
     geo_init(&g, c);
     or_tab T;
-    if (tab_init(&T, g.d, g.n)) return OR_EINVAL;
+    if (tab_init(&T, g.d, g.n, g.M, (const int(*)[3])g.exps)) return OR_EINVAL;
     int d = g.d, M = g.M, NF = g.NF;
     int npts = T.NQ + 2 * d * T.NQF;
     int status = OR_OK;
@@ -1221,6 +1257,21 @@ int or_step(const or_cfg *c, double *w, double *S_prev, double *wig, double *sca
 }
 
 /* basis values phi_l at arbitrary reference points xi[npts][d] -> out[npts][M] */
+/* basis values phi_l at reference points xi[npts][d] -> out[npts][M] for either basis */
+int or_basis_eval_b(int d, int n, int basis, int npts, const double *xi, double *out)
+{
+    int exps[OR_MAXM][3], mode_of[OR_MAXM];
+    if (d < 2 || d > 3 || n < 0 || n > OR_MAXN) return OR_EINVAL;
+    int M = mode_list(d, n, basis, exps, mode_of);
+    for (int i = 0; i < npts; ++i)
+        for (int l = 0; l < M; ++l) {
+            double v = 1.0;
+            for (int a = 0; a < d; ++a) v *= or_pt(exps[l][a], xi[i * d + a]);
+            out[i * M + l] = v;
+        }
+    return OR_OK;
+}
+
 int or_basis_eval(int d, int n, int npts, const double *xi, double *out)
 {
     int Q = n + 1, M = 1;
@@ -1263,7 +1314,7 @@ int or_face_recovery(const or_cfg *c, const double *w, long KL, long KR, int ax,
     or_geo g;
     geo_init(&g, c);
     or_tab T;
-    if (tab_init(&T, g.d, g.n)) return OR_EINVAL;
+    if (tab_init(&T, g.d, g.n, g.M, (const int(*)[3])g.exps)) return OR_EINVAL;
     memset(gt, 0, sizeof(double) * T.NQF * 3 * g.NF);
     face_recovery(&T, &g, w, KL, KR, ax, ut, gt);
     tab_free(&T);

@@ -51,6 +51,7 @@ class Workload:
     # passive tracer (Sec. 3.4): conserved field rho c after the energy, diffusivity eta
     tracer_on: int = 0
     eta: float = 0.0
+    basis: int = 0  # 0 tensor product, 1 total degree l_x + l_y + l_z <= n (Sec. 2.3)
 
     @property
     def ncell(self) -> int:
@@ -58,7 +59,7 @@ class Workload:
 
     @property
     def M(self) -> int:
-        return (self.n + 1) ** self.dim
+        return len(mode_exponents(self.dim, self.n, self.basis))
 
     @property
     def nfields(self) -> int:
@@ -82,6 +83,14 @@ class Workload:
 
     def with_(self, **kw) -> "Workload":
         return replace(self, **kw)
+
+
+def mode_exponents(dim: int, n: int, basis: int = 0) -> np.ndarray:
+    """[M, dim] Legendre degrees of the modes in state order: tensor order with x fastest, all l_a <= n
+    (basis 0) or only l_x + l_y + l_z <= n (basis 1, the paper's total-degree truncation)"""
+    grids = np.meshgrid(*([np.arange(n + 1)] * dim)[::-1], indexing="ij")
+    e = np.stack([g.reshape(-1) for g in grids[::-1]], axis=1)
+    return e[e.sum(1) <= n] if basis == 1 else e
 
 
 # ------------------------------------------------------------------ the five paper-shaped workloads
@@ -151,8 +160,7 @@ def project(wl: Workload, func, q: int | None = None, chunk: int = 1 << 15) -> n
     xi = np.stack([gg.reshape(-1) for gg in grids[::-1]], axis=1)  # [q^d, d], axis 0 fastest
     idx = np.stack([gg.reshape(-1) for gg in np.meshgrid(*([np.arange(q)] * d)[::-1], indexing="ij")[::-1]], 1)
     G = np.prod(g[idx], axis=1)
-    midx = np.stack([gg.reshape(-1) for gg in
-                     np.meshgrid(*([np.arange(wl.n + 1)] * d)[::-1], indexing="ij")[::-1]], 1)  # [M, d]
+    midx = mode_exponents(d, wl.n, wl.basis)  # [M, d]
     phi = np.ones((xi.shape[0], wl.M))
     for a in range(d):
         phi *= B[idx[:, a]][:, midx[:, a]]
@@ -291,8 +299,7 @@ def random_modal_state(wl: Workload, seed: int, amp: float = 0.05, decay: float 
     cell) and higher modes drawn with amplitude amp * decay^(l_x+l_y+l_z) relative to the mean."""
     rng = np.random.default_rng(seed)
     d, n = wl.dim, wl.n
-    midx = np.stack([gg.reshape(-1) for gg in
-                     np.meshgrid(*([np.arange(n + 1)] * d)[::-1], indexing="ij")[::-1]], 1)
+    midx = mode_exponents(d, n, wl.basis)
     scale = decay ** midx.sum(1)
     scale[0] = 0.0
     K = wl.ncell
@@ -300,6 +307,8 @@ def random_modal_state(wl: Workload, seed: int, amp: float = 0.05, decay: float 
     vel0 = [0.3 * rng.uniform(-1, 1, K) for _ in range(d)]
     p0 = 1.0 + 0.3 * rng.uniform(-1, 1, K)
     mean = _cons(wl.gamma, rho0, vel0, p0, alpha_level * rng.uniform(0, 1, K) if wl.av_on else None)
+    if wl.tracer_on:  # rho c with c in [0.2, 1], inserted after the energy
+        mean = np.insert(mean, d + 2, rho0 * rng.uniform(0.2, 1.0, K), axis=0)
     w = np.zeros(wl.shape())
     w[:, :, 0] = mean
     hi = rng.uniform(-1, 1, (wl.nfields, K, wl.M)) * scale[None, None, :] * amp

@@ -9,7 +9,7 @@ def problem(wl, **kw) -> oracle.Problem:
                 bc=tuple(wl.bc[: wl.dim]), gamma=wl.gamma, nu=wl.nu, kappa=wl.kappa, av_on=wl.av_on,
                 positivity_on=wl.positivity_on, cfl=wl.cfl, forcing_on=wl.forcing_on, force_amp=wl.force_amp,
                 force_ts=wl.force_ts, force_dt=wl.force_dt, force_seed=wl.force_seed, tracer_on=wl.tracer_on,
-                eta=wl.eta)
+                eta=wl.eta, basis=wl.basis)
     args.update(kw)
     return oracle.Problem(**args)
 
