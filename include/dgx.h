@@ -11,7 +11,8 @@
  *
  * State layout (host and device, all entry points): float64
  *   w[field][cell][mode],  cell = ix + Nx*(iy + Ny*iz),
- *   mode l = lx + (n+1)*(ly + (n+1)*lz),
+ *   mode l = lx + (n+1)*(ly + (n+1)*lz) (tensor basis; with the total-degree
+ *   basis the same order with the modes lx + ly + lz > n left out),
  *   fields (rho, rho vx, rho vy, [rho vz], e, [rho c], [alpha]) -- rho c with the tracer on.
  * w[f][K][0] is the cell mean (basis normalised so that (1/|K|) int phi_l phi_m = delta).
  *
@@ -52,6 +53,7 @@ enum {
 
 enum { DG_BC_PERIODIC = 0, DG_BC_OUTFLOW = 1 };
 enum { DG_FP64 = 0, DG_FP32_BULK = 1 };
+enum { DG_BASIS_TENSOR = 0, DG_BASIS_TOTAL = 1 };
 
 /* Cartesian grid: dim = 2 or 3; n[a] cells along axis a on [lo[a], hi[a]];
  * bc[a] = DG_BC_PERIODIC or DG_BC_OUTFLOW (the ghost trace equals the
@@ -96,7 +98,17 @@ typedef struct dg_grid {
  *             c rho v and diffused with flux tracer_eta rho grad c through the
  *             recovered gradients of Sec. 3.2; it has no effect on the flow.
  *             Changing it reallocates the state (one more field).  Not
- *             supported in batches. */
+ *             supported in batches.
+ *  basis:     DG_BASIS_TENSOR (default): all products Pt_lx Pt_ly Pt_lz with
+ *             every l_a <= n, (n+1)^d modes; DG_BASIS_TOTAL: the paper's
+ *             truncation l_x + l_y + l_z <= n (Sec. 2.3; (n+1)(n+2)/2 modes in
+ *             2-D, (n+1)(n+2)(n+3)/6 in 3-D), in the same order with the other
+ *             modes left out.  States passed in and out hold those modes only;
+ *             the library keeps them in the tensor layout with the others at
+ *             zero (the same arithmetic per step; no memory saving).  The
+ *             oscillation sensor's high modes become l_x + l_y + l_z = n.
+ *             Changing it reallocates the state.  dg_max_dt_noalloc reads
+ *             tensor-layout states only. */
 typedef struct dg_params {
     int precision;
     int rk_stages;
@@ -109,6 +121,7 @@ typedef struct dg_params {
     unsigned long long force_seed;
     int tracer_on;
     double tracer_eta;
+    int basis;
 } dg_params;
 
 /* Fill p with the defaults listed above (DG_FP64, automatic RK, AV off). */

@@ -82,6 +82,29 @@ __global__ void to_f32_kernel(const double *__restrict__ a, float *__restrict__ 
         b[i] = (float)a[i];
 }
 
+// total-degree basis: the caller's states hold only the modes l_x + l_y + l_z <= n (map[m] = their
+// tensor index); internally every field of a cell keeps the full tensor layout with the other
+// modes at zero.  rows = fields x cells; expand writes into a zeroed tensor array.
+__global__ void td_expand_kernel(const double *__restrict__ src, double *__restrict__ dst, const int *map, int Mapi,
+                                 int M, long long rows)
+{
+    const long long total = rows * Mapi;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / Mapi;
+        dst[r * M + map[i - r * Mapi]] = src[i];
+    }
+}
+
+__global__ void td_compact_kernel(const double *__restrict__ src, double *__restrict__ dst, const int *map, int Mapi,
+                                  int M, long long rows)
+{
+    const long long total = rows * Mapi;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / Mapi;
+        dst[i] = src[r * M + map[i - r * Mapi]];
+    }
+}
+
 // dt from the per-block maxima of the prologue (Eq. timestep), or a fixed dt
 __global__ void dt_kernel(const double *partial, int nblk, double fixed_dt, double cfl, double hmin, int P,
                           double *dtp, int advance, int *status)
@@ -210,6 +233,11 @@ struct dg_handle {
     long long ftab_off[3] = {0, 0, 0};
     int forced_last = 0;  // the last enqueued step ran the driving kernels
 
+    // total-degree basis (Sec. 2.3): modes seen by the caller, their tensor indices, staging buffer
+    int Mapi = 1;
+    int *d_modemap = nullptr;
+    double *stage = nullptr;  // [fields][cells][Mapi] for host transfers
+
     cudaEvent_t ev[kMaxEvents] = {nullptr};  // per-launch timing events of dg_step_timed
 
     std::string err;
@@ -268,6 +296,28 @@ void free_buffers(dg_t *h)
     cudaFree(h->ftab);
     h->fstate = h->smodes = nullptr;
     h->force = h->ftab = nullptr;
+    cudaFree(h->d_modemap);
+    cudaFree(h->stage);
+    h->d_modemap = nullptr;
+    h->stage = nullptr;
+}
+
+bool total_degree(const dg_t *h) { return h->p.basis == DG_BASIS_TOTAL; }
+size_t nw_api(const dg_t *h) { return (size_t)h->nf * h->ncell * h->Mapi; }
+
+int expand_state(dg_t *h, const double *src, double *dst)
+{
+    CK(h, cudaMemsetAsync(dst, 0, h->nw * sizeof(double), h->stream));
+    td_expand_kernel<<<1024, 256, 0, h->stream>>>(src, dst, h->d_modemap, h->Mapi, h->M, (long long)h->nf * h->ncell);
+    CK(h, cudaGetLastError());
+    return DG_OK;
+}
+
+int compact_state(dg_t *h, const double *src, double *dst)
+{
+    td_compact_kernel<<<1024, 256, 0, h->stream>>>(src, dst, h->d_modemap, h->Mapi, h->M, (long long)h->nf * h->ncell);
+    CK(h, cudaGetLastError());
+    return DG_OK;
 }
 
 // driving buffers (allocated while forcing is on; the OU state starts with no update applied)
@@ -361,6 +411,20 @@ int alloc_buffers(dg_t *h)
     if (!st) st = al((void **)&h->partial, 2 * (size_t)h->partial_cap * sizeof(double));
     if (!st) st = al((void **)&h->sums, ((size_t)kSumBlocks * h->nc + h->nc) * sizeof(double));
     if (!st) st = al((void **)&h->status, sizeof(int));
+    // modes seen by the caller: all tensor modes, or those with l_x + l_y + l_z <= n
+    std::vector<int> modemap;
+    for (int t = 0; t < h->M; ++t) {
+        const int lx = t % h->Q, ly = (t / h->Q) % h->Q, lz = h->dim == 3 ? t / (h->Q * h->Q) : 0;
+        if (h->p.basis != DG_BASIS_TOTAL || lx + ly + lz <= h->degree) modemap.push_back(t);
+    }
+    h->Mapi = (int)modemap.size();
+    if (!st && total_degree(h)) {
+        st = al((void **)&h->d_modemap, modemap.size() * sizeof(int));
+        if (!st) st = al((void **)&h->stage, nw_api(h) * sizeof(double));
+        if (!st && cudaMemcpy(h->d_modemap, modemap.data(), modemap.size() * sizeof(int), cudaMemcpyHostToDevice) !=
+                       cudaSuccess)
+            st = fail(h, DG_ECUDA, "mode map upload");
+    }
     if (st) {
         free_buffers(h);
         return st;
@@ -399,6 +463,7 @@ void base_stage_args(const dg_t *h, StageArgs &a)
     a.ns_on = (h->nu > 0.0 || h->kappa > 0.0) ? 1 : 0;
     a.tracer_on = h->p.tracer_on;
     a.eta = h->p.tracer_eta;
+    a.total_degree = total_degree(h) ? 1 : 0;
     a.av_on = h->p.av_on;
     a.av_scale = h->p.av_scale;
     a.f_v = h->p.f_v;
@@ -442,6 +507,7 @@ cudaError_t launch_prologue_any(const dg_t *h, int update_sensor)
     a.s_on = h->p.s_onset / ((double)(h->degree + 1) * (h->degree + 1));
     a.partial = h->partial;
     a.status = h->status;
+    a.total_degree = total_degree(h) ? 1 : 0;
     if (h->dim == 2)
         return fp32(h) ? launch_prologue_2d_f32(h->degree, a, h->tf, h->stream)
                        : launch_prologue_2d_f64(h->degree, a, h->td, h->stream);
@@ -630,6 +696,38 @@ int refresh_hi(dg_t *h)
     return DG_OK;
 }
 
+// right-hand side in the internal (tensor) layout
+int rhs_tensor(dg_t *h, double *dev_out)
+{
+    StageArgs a;
+    base_stage_args(h, a);
+    a.ubase = fp32(h) ? (const void *)h->Uhi[h->cur] : (const void *)h->U[h->cur];
+    a.din = nullptr;
+    a.mode = 0;
+    a.rhs_out = dev_out;
+    if (h->p.forcing_on) {
+        // the field of the current driving state, without advancing it
+        CK(h, launch_forcing_update(h->fm, h->dim, h->p.force_dt, h->p.force_ts, h->p.force_seed, 0, h->fstate,
+                                    h->dtp + 2, h->smodes, h->status, h->stream));
+        CK(h, launch_forcing_eval_any(h));
+    }
+    CK(h, launch_stage_any(h, a));
+    return DG_OK;
+}
+
+int ensure_rhs_tmp(dg_t *h)
+{
+    if (h->rhs_tmp) return DG_OK;
+    cudaError_t e = cudaMalloc((void **)&h->rhs_tmp, h->nw * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->rhs_tmp = nullptr;
+        return fail(h, DG_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+    }
+    return DG_OK;
+}
+
+
 }  // namespace
 
 extern "C" {
@@ -668,6 +766,7 @@ int dg_default_params(dg_params *p)
     p->force_seed = 0;
     p->tracer_on = 0;
     p->tracer_eta = 0.0;
+    p->basis = DG_BASIS_TENSOR;
     return DG_OK;
 }
 
@@ -749,8 +848,9 @@ int dg_set_params(dg_t *h, const dg_params *p)
         return fail(h, DG_EINVAL, "forcing needs force_ts > 0, force_dt > 0, force_amp >= 0");
     if ((p->tracer_on != 0 && p->tracer_on != 1) || !(p->tracer_eta >= 0.0))
         return fail(h, DG_EINVAL, "tracer_on must be 0 or 1 and tracer_eta >= 0");
-    const bool realloc =
-        p->precision != h->p.precision || p->av_on != h->p.av_on || p->tracer_on != h->p.tracer_on;
+    if (p->basis != DG_BASIS_TENSOR && p->basis != DG_BASIS_TOTAL) return fail(h, DG_EINVAL, "unknown basis");
+    const bool realloc = p->precision != h->p.precision || p->av_on != h->p.av_on ||
+                         p->tracer_on != h->p.tracer_on || p->basis != h->p.basis;
     h->p = *p;
     if (h->graph) {
         cudaGraphExecDestroy(h->graph);
@@ -772,7 +872,7 @@ int dg_sizes(const dg_t *h, int *nfields, int *nmodes, long long *ncells)
 {
     if (!h) return DG_EINVAL;
     if (nfields) *nfields = h->nf;
-    if (nmodes) *nmodes = h->M;
+    if (nmodes) *nmodes = h->Mapi;
     if (ncells) *ncells = h->ncell;
     return DG_OK;
 }
@@ -787,7 +887,13 @@ int dg_set_stream(dg_t *h, void *stream)
 int dg_set_state(dg_t *h, const double *host_w)
 {
     if (!h || !host_w) return DG_EINVAL;
-    CK(h, cudaMemcpyAsync(h->U[h->cur], host_w, h->nw * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (total_degree(h)) {
+        CK(h, cudaMemcpyAsync(h->stage, host_w, nw_api(h) * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        int st = expand_state(h, h->stage, h->U[h->cur]);
+        if (st) return st;
+    } else {
+        CK(h, cudaMemcpyAsync(h->U[h->cur], host_w, h->nw * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    }
     int st = refresh_hi(h);
     if (st) return st;
     CK(h, cudaStreamSynchronize(h->stream));
@@ -797,57 +903,60 @@ int dg_set_state(dg_t *h, const double *host_w)
 int dg_set_state_device(dg_t *h, const double *dev_w)
 {
     if (!h || !dev_w) return DG_EINVAL;
-    CK(h, cudaMemcpyAsync(h->U[h->cur], dev_w, h->nw * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    if (total_degree(h)) {
+        int st = expand_state(h, dev_w, h->U[h->cur]);
+        if (st) return st;
+    } else {
+        CK(h, cudaMemcpyAsync(h->U[h->cur], dev_w, h->nw * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    }
     return refresh_hi(h);
 }
 
 int dg_get_state(dg_t *h, double *host_w)
 {
     if (!h || !host_w) return DG_EINVAL;
-    CK(h, cudaMemcpyAsync(host_w, h->U[h->cur], h->nw * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (total_degree(h)) {
+        int st = compact_state(h, h->U[h->cur], h->stage);
+        if (st) return st;
+        CK(h, cudaMemcpyAsync(host_w, h->stage, nw_api(h) * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    } else {
+        CK(h, cudaMemcpyAsync(host_w, h->U[h->cur], h->nw * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    }
     return check_status(h);
 }
 
 int dg_get_state_device(dg_t *h, double *dev_w)
 {
     if (!h || !dev_w) return DG_EINVAL;
+    if (total_degree(h)) return compact_state(h, h->U[h->cur], dev_w);
     CK(h, cudaMemcpyAsync(dev_w, h->U[h->cur], h->nw * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     return DG_OK;
 }
 
+
 int dg_rhs_device(dg_t *h, double *dev_out)
 {
     if (!h || !dev_out) return DG_EINVAL;
-    StageArgs a;
-    base_stage_args(h, a);
-    a.ubase = fp32(h) ? (const void *)h->Uhi[h->cur] : (const void *)h->U[h->cur];
-    a.din = nullptr;
-    a.mode = 0;
-    a.rhs_out = dev_out;
-    if (h->p.forcing_on) {
-        // the field of the current driving state, without advancing it
-        CK(h, launch_forcing_update(h->fm, h->dim, h->p.force_dt, h->p.force_ts, h->p.force_seed, 0, h->fstate,
-                                    h->dtp + 2, h->smodes, h->status, h->stream));
-        CK(h, launch_forcing_eval_any(h));
-    }
-    CK(h, launch_stage_any(h, a));
-    return DG_OK;
+    if (!total_degree(h)) return rhs_tensor(h, dev_out);
+    int st = ensure_rhs_tmp(h);
+    if (!st) st = rhs_tensor(h, h->rhs_tmp);
+    if (!st) st = compact_state(h, h->rhs_tmp, dev_out);
+    return st;
 }
 
 int dg_rhs(dg_t *h, double *host_out)
 {
     if (!h || !host_out) return DG_EINVAL;
-    if (!h->rhs_tmp) {
-        cudaError_t e = cudaMalloc((void **)&h->rhs_tmp, h->nw * sizeof(double));
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            h->rhs_tmp = nullptr;
-            return fail(h, DG_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
-        }
-    }
-    int st = dg_rhs_device(h, h->rhs_tmp);
+    int st = ensure_rhs_tmp(h);
+    if (!st) st = rhs_tensor(h, h->rhs_tmp);
     if (st) return st;
-    CK(h, cudaMemcpyAsync(host_out, h->rhs_tmp, h->nw * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (total_degree(h)) {
+        st = compact_state(h, h->rhs_tmp, h->stage);
+        if (st) return st;
+        CK(h, cudaMemcpyAsync(host_out, h->stage, nw_api(h) * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    } else {
+        CK(h, cudaMemcpyAsync(host_out, h->rhs_tmp, h->nw * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    }
     return check_status(h);
 }
 

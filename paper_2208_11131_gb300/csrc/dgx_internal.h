@@ -64,6 +64,7 @@ struct StageArgs {
     int ns_on;  // nu > 0 or kappa > 0
     int tracer_on;  // passive tracer field rho c after the energy (Sec. 3.4)
     double eta;     // its diffusivity
+    int total_degree;  // basis of modes l_x + l_y + l_z <= n (Sec. 2.3): the others are kept at zero
     int av_on;
     double av_scale, f_v, f_tau;
     int nf;  // fields incl. alpha
@@ -160,6 +161,7 @@ struct PrologueArgs {
     double f_w, s_on;
     double *partial;  // [blocks][2] max c_s, max |v|
     int *status;
+    int total_degree;  // sensor: high modes are l_x + l_y + l_z = n instead of some l_a = n
 };
 
 // Arguments of the positivity-limiter kernel (Sec. 4.2), run after a stage.

@@ -332,7 +332,9 @@ __global__ void __launch_bounds__(256) prologue_kernel(const PrologueArgs A, con
             for (int l = 0; l < NP; ++l) {
                 const Real w = sU[c * NP + l];  // density field (f = 0)
                 const int l0 = l % Q, l1 = (l / Q) % Q, l2 = DIM == 3 ? l / (Q * Q) : 0;
-                const bool top = N > 0 && (l0 == N || l1 == N || (DIM == 3 && l2 == N));
+                // the modes the degree-(n-1) basis lacks (Sec. 4.1)
+                const bool top = N > 0 && (A.total_degree ? (l0 + l1 + l2 == N)
+                                                          : (l0 == N || l1 == N || (DIM == 3 && l2 == N)));
                 all += w * w;
                 if (top) hi += w * w;
             }

@@ -372,7 +372,9 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
 #pragma unroll
                 for (int l = 0; l < NP; ++l) {
                     const int l0 = l % Q, l1 = (l / Q) % Q, l2 = DIM == 3 ? l / (Q * Q) : 0;
-                    const bool top = N > 0 && (l0 == N || l1 == N || (DIM == 3 && l2 == N));
+                    // the modes the degree-(n-1) basis lacks (Sec. 4.1)
+                    const bool top = N > 0 && (A.total_degree ? (l0 + l1 + l2 == N)
+                                                              : (l0 == N || l1 == N || (DIM == 3 && l2 == N)));
                     all += w0[l] * w0[l];
                     if (top) hi += w0[l] * w0[l];
                 }
@@ -778,6 +780,13 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                     L[l] = acc;
                 }
                 const size_t gi = ((size_t)f * A.ncell + g) * NP + (size_t)r * Q;
+                if (A.total_degree) {
+                    // total-degree basis: modes with l_x + l_y + l_z > n are not in the space and stay 0
+                    const int lyz = r % Q + (DIM == 3 ? r / Q : 0);
+#pragma unroll
+                    for (int l = 0; l < Q; ++l)
+                        if (l + lyz > N) L[l] = Real(0);
+                }
                 if (A.mode == 0) {
 #pragma unroll
                     for (int l = 0; l < Q; ++l) A.rhs_out[gi + l] = (double)L[l];

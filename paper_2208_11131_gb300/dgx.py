@@ -44,7 +44,10 @@ class dg_params(ctypes.Structure):
                 ("f_tau", ctypes.c_double), ("f_w", ctypes.c_double), ("s_onset", ctypes.c_double),
                 ("positivity_on", ctypes.c_int), ("forcing_on", ctypes.c_int), ("force_amp", ctypes.c_double),
                 ("force_ts", ctypes.c_double), ("force_dt", ctypes.c_double), ("force_seed", ctypes.c_ulonglong),
-                ("tracer_on", ctypes.c_int), ("tracer_eta", ctypes.c_double)]
+                ("tracer_on", ctypes.c_int), ("tracer_eta", ctypes.c_double), ("basis", ctypes.c_int)]
+
+DG_BASIS_TENSOR = 0
+DG_BASIS_TOTAL = 1
 
 FORCING_STATE = 97  # DG_FORCING_STATE
 
@@ -293,6 +296,7 @@ class Simulation:
         p.cfl = wl.cfl if cfl is None else cfl
         p.av_on = int(wl.av_on)
         p.positivity_on = int(getattr(wl, "positivity_on", 0))
+        p.basis = int(getattr(wl, "basis", 0))
         if getattr(wl, "tracer_on", 0):
             p.tracer_on = 1
             p.tracer_eta = float(wl.eta)
