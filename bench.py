@@ -49,16 +49,35 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-extras", action="store_true", help="skip the fp64 side run, e2e and cpu baseline")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched 64-member ensemble measurement")
+    ap.add_argument("--workload", default="shear_layer_256", choices=sorted(WORKLOADS),
+                    help="workload of the main measurement (the extras always use the default one)")
     return ap.parse_args()
 
 
-def workload():
+# name -> (label, workload factory, initial modes); the default is the benchmark workload
+WORKLOADS = {
+    "shear_layer_256": ("ns_shear_layer_2d_256x256_deg3_av",
+                        lambda inputs: inputs.c2_shear_layer(N=256, n=3),
+                        lambda inputs, wl: inputs.project(wl, inputs.shear_layer_ic(wl))),
+    "turbulence_box_64": ("driven_turbulence_3d_64cubed_deg3_av_ns_forcing",
+                          lambda inputs: inputs.c4_turbulence_box(N=64, n=3),
+                          lambda inputs, wl: inputs.rest_state(wl)),
+    "turbulence_box_128": ("driven_turbulence_3d_128cubed_deg3_av_ns_forcing",
+                           lambda inputs: inputs.c4_turbulence_box(N=128, n=3),
+                           lambda inputs, wl: inputs.rest_state(wl)),
+}
+DEFAULT_WORKLOAD = "shear_layer_256"
+
+
+def workload(name: str = DEFAULT_WORKLOAD):
     from paper_2208_11131_gb300 import inputs
-    return inputs.c2_shear_layer(N=256, n=3)
+    label, make, ic = WORKLOADS[name]
+    wl = make(inputs)
+    return wl, (lambda: ic(inputs, wl)), label
 
 
-def config_of(wl, extra=None):
-    cfg = {"workload": "ns_shear_layer_2d_256x256_deg3_av", "cells": list(wl.N[:2]), "degree": wl.n,
+def config_of(wl, extra=None, label=WORKLOADS[DEFAULT_WORKLOAD][0]):
+    cfg = {"workload": label, "cells": list(wl.N[:wl.dim]), "degree": wl.n,
            "fields": wl.nfields, "conserved_dofs": wl.dofs, "rk_stages": 5, "nu": wl.nu, "kappa": wl.kappa,
            "gamma": wl.gamma, "cfl": wl.cfl, "l2": "flushed before every timed step (256 MiB device write)"}
     if extra:
@@ -229,8 +248,8 @@ def reference_arm(args, rank, ws):
         return
     import numpy as np  # noqa: F401
     from paper_2208_11131_gb300 import inputs
-    wl = workload()
-    w0 = inputs.project(wl, inputs.shear_layer_ic(wl))
+    wl, ic, _ = workload()
+    w0 = ic()
     run_oracle_steps(wl, w0, args.warmup)
     secs, done, cores = run_oracle_steps(wl, w0, args.steps)
     units = wl.dofs * 5 * done
@@ -361,8 +380,9 @@ def dgx_arm(args, rank, ws, local):
     torch.cuda.set_device(local)
     B.build()
     dgx.lib()
-    wl = workload()
-    w0 = inputs.project(wl, inputs.shear_layer_ic(wl))
+    wl, ic, label = workload(args.workload)
+    w0 = ic()
+    default = args.workload == DEFAULT_WORKLOAD
     fp32 = args.precision == "fp32"
     prec = dgx.DG_FP32_BULK if fp32 else dgx.DG_FP64
     stream = torch.cuda.current_stream().cuda_stream
@@ -401,7 +421,7 @@ def dgx_arm(args, rank, ws, local):
     achieved = stage_bytes * args.steps / (stage_ms / 1e3) / 1e9
     peaks, peak_kind = measured_peaks()
     peak = float(peaks["hbm_gbs"])
-    key = f"stage_kernel|ns_shear_layer_2d_256x256_deg3_av|{'fp32' if fp32 else 'fp64'}"
+    key = f"stage_kernel|{label}|{'fp32' if fp32 else 'fp64'}"
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic_for(key), "peak_source": f"{peak_kind} hbm_gbs",
             "algorithmic_bytes_per_launch": stage_bytes / 5,
@@ -410,15 +430,16 @@ def dgx_arm(args, rank, ws, local):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64", "data": "synthetic",
-            "config": config_of(wl, {"precision": "fp32-bulk (fp64 state and RK accumulation)" if fp32 else "fp64",
-                                     "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"}),
+            "config": config_of(wl, label=label,
+                                extra={"precision": "fp32-bulk (fp64 state and RK accumulation)" if fp32 else "fp64",
+                                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"}),
             "roofline": roof, "clocks": clk,
             # launches the library made per step: folded-away slots of dg_step_timed read 0
             "gpu_launches": args.steps * sum(1 for i in range(nl) if np.mean([x[i] for x in per_launch]) > 0),
             "launch_ms_mean": [float(np.mean([x[i] for x in per_launch])) for i in range(nl)],
             "wall_ms_per_step": 1e3 * t_wall / args.steps}
 
-    if not args.no_extras:
+    if not args.no_extras and default:
         # end to end through the public C ABI with pinned host buffers: H2D state, one step, D2H state
         host_in = torch.from_numpy(w0).pin_memory()
         host_out = torch.empty_like(host_in).pin_memory()
@@ -467,9 +488,9 @@ def dgx_arm(args, rank, ws, local):
                                     "kind": "oracle",
                                     "sample": f"full 256x256 grid, {done} whole FP64 SSP(5,4) steps"}
     sim.close()
-    if not args.no_ensemble:
+    if not args.no_ensemble and default:
         line["ensemble"] = ensemble_measurement(dgx, inputs, torch, stream, steps=20, warmup=3)
-    if not args.no_extras and rank == 0:
+    if not args.no_extras and default and rank == 0:
         line["other_paths"] = side_workloads(dgx, inputs, l1_error_of, torch, stream, flush)
     if rank == 0:
         print(json.dumps(line), flush=True)
