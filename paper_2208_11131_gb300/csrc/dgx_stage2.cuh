@@ -708,30 +708,65 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
         if constexpr (DIM == 3) flux_axis(std::integral_constant<int, 2>{});
         __syncthreads();
 
-        // ---- nodal residual of the conserved fields: weak divergence + lift
-        for (int idx = tid; idx < NC * TC * NP; idx += nth) {
-            const int n = idx % NP;
-            const int fc = idx / NP;
-            const int c = fc % TC, f = fc / TC;
-            if (sG[c] < 0) continue;
-            const int cc[3] = {c % TX, (c / TX) % TY, c / (TX * TY)};
-            Real r = Real(0);
+        // ---- nodal residual of the conserved fields: weak divergence + lift, one pass per axis over
+        // the lines of Q nodes along it, all Q outputs of a line at once (the operator tables are
+        // kernel-parameter operands); the first pass starts from the driving source, if any, the
+        // later ones add to the stored partial sums
+        auto residual_axis = [&](auto axc) {
+            constexpr int a = decltype(axc)::value;
+            constexpr int Sa = S::S(a);
+            constexpr int LPC = NP / Q;  // lines per cell along a = face points per face
+            for (int idx = tid; idx < NC * TC * LPC; idx += nth) {
+                const int k = idx % LPC;  // transverse node in the face numbering
+                const int fc = idx / LPC;
+                const int c = fc % TC, f = fc / TC;
+                if (sG[c] < 0) continue;
+                const int cx = c % TX, cy = (c / TX) % TY, cz = c / (TX * TY);
+                const int ca = a == 0 ? cx : (a == 1 ? cy : cz);
+                const int fl = S::FOFF(a) + ca + (S::T(a) + 1) * S::trans(a, cx, cy, cz);
+                const Real fL = sFh[(f * NFACE + fl) * NPF + k];
+                const Real fR = sFh[(f * NFACE + fl + 1) * NPF + k];
+                const int n0 = S::knode(a, 0, k);
+                const Real *Fp = sF + ((a * NC + f) * TC + c) * NPS + n0;
+                Real *rp = sR + fc * NPS + n0;
+                Real F[Q], r[Q];
+                if constexpr (a == 0) {
+                    ld_line<Q, VEC>(Fp, F);
+                    if (A.force && f > 0 && f <= DIM + 1) {  // momentum and energy
+                        ld_line<Q, VEC>(rp, r);
+                    } else {
 #pragma unroll
-            for (int a = 0; a < DIM; ++a) {
-                const int Sa = S::S(a);
-                const int i = (n / Sa) % Q;
-                const Real *Fp = sF + ((a * NC + f) * TC + c) * NPS + (n - i * Sa);
+                        for (int i = 0; i < Q; ++i) r[i] = Real(0);
+                    }
+                } else {
 #pragma unroll
-                for (int m = 0; m < Q; ++m) r = fma(tWd[i * Q + m], Fp[m * Sa], r);
-                const int tt = S::trans(a, cc[0], cc[1], cc[2]);
-                const int fl = S::FOFF(a) + cc[a] + (S::T(a) + 1) * tt;
-                const int k = S::ktrans(a, n);
-                r = fma(tLm[i], sFh[(f * NFACE + fl) * NPF + k], r);
-                r = fma(-tLp[i], sFh[(f * NFACE + fl + 1) * NPF + k], r);
+                    for (int m = 0; m < Q; ++m) {
+                        F[m] = Fp[m * Sa];
+                        r[m] = rp[m * Sa];
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    Real acc = r[i];
+#pragma unroll
+                    for (int m = 0; m < Q; ++m) acc = fma(Tg.Wd[i][m], F[m], acc);
+                    acc = fma(Tg.Lm[i], fL, acc);
+                    r[i] = fma(-Tg.Lp[i], fR, acc);
+                }
+                if constexpr (a == 0) {
+                    st_line<Q, VEC>(rp, r);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) rp[i * Sa] = r[i];
+                }
             }
-            const int ri = fc * NPS + n;
-            if (A.force && f > 0 && f <= DIM + 1) r += sR[ri];  // momentum and energy
-            sR[ri] = r;
+        };
+        residual_axis(std::integral_constant<int, 0>{});
+        __syncthreads();
+        residual_axis(std::integral_constant<int, 1>{});
+        if constexpr (DIM == 3) {
+            __syncthreads();
+            residual_axis(std::integral_constant<int, 2>{});
         }
         __syncthreads();
 
