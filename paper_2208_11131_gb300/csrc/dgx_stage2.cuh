@@ -89,6 +89,10 @@ struct Stage2Plan {
                   "cell arrays must start on 16-byte boundaries");
 };
 
+// the Q values of a cell along axis A starting at p (stride S): one vector access along x
+template <int A, int Q, int VEC, int S, typename T>
+__device__ __forceinline__ void ld_axis_line(const T *p, T (&w)[Q]);
+
 // one x-line of Q contiguous values from / to shared or global memory with the widest aligned
 // accesses (VEC bytes; the caller guarantees VEC alignment of p)
 template <int Q, int VEC, typename T>
@@ -120,6 +124,17 @@ __device__ __forceinline__ void ld_line(const T *p, T (&w)[Q])
     } else {
 #pragma unroll
         for (int m = 0; m < Q; ++m) w[m] = p[m];
+    }
+}
+
+template <int A, int Q, int VEC, int S, typename T>
+__device__ __forceinline__ void ld_axis_line(const T *p, T (&w)[Q])
+{
+    if constexpr (A == 0) {
+        ld_line<Q, VEC>(p, w);
+    } else {
+#pragma unroll
+        for (int m = 0; m < Q; ++m) w[m] = p[m * S];
     }
 }
 
@@ -576,11 +591,12 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                         const int sr = pp < V[a] ? cr[0] + TX * (cr[1] + TY * cr[2]) : S::HOFF(a, 1) + t;
                         if (sG[sl] < 0 || sG[sr] < 0) continue;
                         const int base = S::knode(a, 0, k);
-                        const Real *pl = sU + (f * NSLOT + sl) * NPS + base;
-                        const Real *pr = sU + (f * NSLOT + sr) * NPS + base;
+                        Real lv[Q], rv[Q];
+                        ld_axis_line<a, Q, VEC, Sa>(sU + (f * NSLOT + sl) * NPS + base, lv);
+                        ld_axis_line<a, Q, VEC, Sa>(sU + (f * NSLOT + sr) * NPS + base, rv);
                         Real acc = Real(0);
 #pragma unroll
-                        for (int m = 0; m < Q; ++m) acc = fma(Tg.Cm[m], pl[m * Sa], fma(Tg.Cp[m], pr[m * Sa], acc));
+                        for (int m = 0; m < Q; ++m) acc = fma(Tg.Cm[m], lv[m], fma(Tg.Cp[m], rv[m], acc));
                         sUt[(f * NFACE + S::FOFF(a) + fl) * NPF + k] = acc;
                     }
                 };
@@ -612,7 +628,7 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
             cr[a] = pp;
             const int sl = pp > 0 ? cl[0] + TX * (cl[1] + TY * cl[2]) : S::HOFF(a, 0) + t;
             const int sr = pp < V[a] ? cr[0] + TX * (cr[1] + TY * cr[2]) : S::HOFF(a, 1) + t;
-            const int Sa = S::S(a);
+            constexpr int Sa = S::S(a);
             const int base = S::knode(a, 0, k);
             Real Fh[NC];
             if (sG[sl] < 0 || sG[sr] < 0) {
@@ -622,43 +638,43 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                 Real u[NC], v[3], rho, pr_, cs;
 #pragma unroll
                 for (int f = 0; f < NC; ++f) {
-                    const Real *q = sU + (f * NSLOT + si) * NPS + base;
+                    Real qv[Q];
+                    ld_axis_line<a, Q, VEC, Sa>(sU + (f * NSLOT + si) * NPS + base, qv);
                     Real acc = Real(0);
 #pragma unroll
-                    for (int m = 0; m < Q; ++m) acc = fma(right_in ? Tg.Lm[m] : Tg.Lp[m], q[m * Sa], acc);
+                    for (int m = 0; m < Q; ++m) acc = fma(right_in ? Tg.Lm[m] : Tg.Lp[m], qv[m], acc);
                     u[f] = acc;
                 }
                 if (!primitives<DIM>(u, gamma, rho, v, pr_, cs)) bad = 1;
                 euler_flux<DIM, TR>(u, v, pr_, a, Fh);
             } else {
-                Real uL[NC + 1], uR[NC + 1];
+                // traces of both sides and, for the dissipative flux, the recovered normal derivative,
+                // from one load of each side's line normal to the face
+                Real uL[NC + 1], uR[NC + 1], dn[NC];
+                const Real sc = inv_f * inv_h[a];
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
-                    const Real *ql = sU + (f * NSLOT + sl) * NPS + base;
-                    const Real *qr = sU + (f * NSLOT + sr) * NPS + base;
+                    Real lv[Q], rv[Q];
+                    ld_axis_line<a, Q, VEC, Sa>(sU + (f * NSLOT + sl) * NPS + base, lv);
+                    ld_axis_line<a, Q, VEC, Sa>(sU + (f * NSLOT + sr) * NPS + base, rv);
                     Real al = Real(0), ar = Real(0);
 #pragma unroll
                     for (int m = 0; m < Q; ++m) {
-                        al = fma(Tg.Lp[m], ql[m * Sa], al);
-                        ar = fma(Tg.Lm[m], qr[m * Sa], ar);
+                        al = fma(Tg.Lp[m], lv[m], al);
+                        ar = fma(Tg.Lm[m], rv[m], ar);
                     }
                     uL[f] = al;
                     uR[f] = ar;
+                    if (GRAD && f < NC) {
+                        Real acc = Real(0);
+#pragma unroll
+                        for (int m = 0; m < Q; ++m) acc = fma(Tg.Dm[m], lv[m], fma(Tg.Dp[m], rv[m], acc));
+                        dn[f] = acc * sc;
+                    }
                 }
                 Real cL, cR;  // trace sound speeds, reused by the artificial viscosity below
                 if (!hllc<DIM, TR>(uL, uR, gamma, a, Fh, cL, cR)) bad = 1;
                 if (GRAD) {
-                    Real dn[NC];
-                    const Real sc = inv_f * inv_h[a];
-#pragma unroll
-                    for (int f = 0; f < NC; ++f) {
-                        const Real *ql = sU + (f * NSLOT + sl) * NPS + base;
-                        const Real *qr = sU + (f * NSLOT + sr) * NPS + base;
-                        Real acc = Real(0);
-#pragma unroll
-                        for (int m = 0; m < Q; ++m) acc = fma(Tg.Dm[m], ql[m * Sa], fma(Tg.Dp[m], qr[m * Sa], acc));
-                        dn[f] = acc * sc;
-                    }
                     if (NS) {
                         Real ut[NC], grd[DIM][NC];
                         const int k0 = k % Q, k1 = k / Q;
