@@ -343,8 +343,15 @@ __global__ void __launch_bounds__(256) prologue_kernel(const PrologueArgs A, con
             // S is floored four decades below the onset threshold: below that its value is rounding
             // noise of the higher modes, and a log of noise would turn into a source of size noise / dt
             const double s_floor = 1e-4 * A.s_on;
-            if (step > 0.0 && dt_prev > 0.0)
-                dlog = (log(fmax(Sk, s_floor)) - log(fmax(A.S_prev[g], s_floor))) / dt_prev;
+            if (step > 0.0 && dt_prev > 0.0) {
+                if constexpr (sizeof(Real) == 4) {  // FP32 sensor: its logarithm in FP32 as well
+                    const float sf = (float)s_floor;
+                    dlog = (double)((logf(fmaxf((float)Sk, sf)) - logf(fmaxf((float)A.S_prev[g], sf))) /
+                                    (float)dt_prev);
+                } else {
+                    dlog = (log(fmax(Sk, s_floor)) - log(fmax(A.S_prev[g], s_floor))) / dt_prev;
+                }
+            }
             A.wig[g] = (Sk > A.s_on) ? A.f_w * fmax(0.0, dlog) : 0.0;
             A.S_prev[g] = Sk;
         }

@@ -397,8 +397,17 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                 const double dt_prev = A.dtp[0], step = A.dtp[1];
                 const double s_floor = 1e-4 * A.s_on;
                 double dlog = 0.0;
-                if (step > 0.0 && dt_prev > 0.0)
-                    dlog = (log(fmax(Sk, s_floor)) - log(fmax(A.S_prev[g], s_floor))) / dt_prev;
+                if (step > 0.0 && dt_prev > 0.0) {
+                    if constexpr (sizeof(Real) == 4) {
+                        // the sensor of the FP32 modes carries FP32 precision: take its logarithm in FP32
+                        // (FP64 arithmetic is a small fraction of the FP32 rate on this part)
+                        const float sf = (float)s_floor;
+                        dlog = (double)((logf(fmaxf((float)Sk, sf)) - logf(fmaxf((float)A.S_prev[g], sf))) /
+                                        (float)dt_prev);
+                    } else {
+                        dlog = (log(fmax(Sk, s_floor)) - log(fmax(A.S_prev[g], s_floor))) / dt_prev;
+                    }
+                }
                 const double wg = (Sk > A.s_on) ? A.f_w * fmax(0.0, dlog) : 0.0;
                 A.wig_w[g] = wg;
                 A.S_prev[g] = Sk;
