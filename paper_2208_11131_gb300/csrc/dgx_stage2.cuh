@@ -278,26 +278,27 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
         __syncthreads();
         if constexpr (!PF) return;  // without prefetch buffers the tile is loaded at the top of its iteration
         constexpr int PER = PL::CELL_BYTES / PL::CHUNK;  // chunks per (field, cell)
-        constexpr int TOTAL = NF * NSLOT * PER;
-        for (int idx = tid; idx < TOTAL; idx += nth) {
-            const int c = idx % PER;
-            const int fs = idx / PER;
-            const int slot = fs % NSLOT, f = fs / NSLOT;
+        // one (slot, chunk) pair per thread and pass, all fields by a constant stride
+        const size_t gfield = (size_t)T.ncell * NP * sizeof(Real);          // bytes between fields
+        constexpr size_t sfield = (size_t)NSLOT * NPS * sizeof(Real);
+        for (int p = tid; p < NSLOT * PER; p += nth) {
+            const int slot = p / PER, c = p % PER;
             const int g = sG[slot];
             if (g < 0) continue;
-            const size_t gbyte = (((size_t)f * T.ncell + g) * NP) * sizeof(Real) + (size_t)c * PL::CHUNK;
-            const size_t sbyte = ((size_t)(f * NSLOT + slot) * NPS) * sizeof(Real) + (size_t)c * PL::CHUNK;
-            const char *gu = reinterpret_cast<const char *>(ub) + gbyte;
-            char *su = reinterpret_cast<char *>(sIn0) + sbyte;
-            if (PL::CHUNK == 16) cp_async_16(su, gu);
-            else if (PL::CHUNK == 8) cp_async_8(su, gu);
-            else cp_async_4(su, gu);
-            if (di) {
-                const char *gd = reinterpret_cast<const char *>(di) + gbyte;
-                char *sd = reinterpret_cast<char *>(sIn1) + sbyte;
-                if (PL::CHUNK == 16) cp_async_16(sd, gd);
-                else if (PL::CHUNK == 8) cp_async_8(sd, gd);
-                else cp_async_4(sd, gd);
+            const char *gu = reinterpret_cast<const char *>(ub) + (size_t)g * NP * sizeof(Real) + (size_t)c * PL::CHUNK;
+            char *su = reinterpret_cast<char *>(sIn0) + (size_t)slot * NPS * sizeof(Real) + (size_t)c * PL::CHUNK;
+            const char *gd = di ? reinterpret_cast<const char *>(di) + (gu - reinterpret_cast<const char *>(ub)) : nullptr;
+            char *sd = reinterpret_cast<char *>(sIn1) + (su - reinterpret_cast<char *>(sIn0));
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                if (PL::CHUNK == 16) cp_async_16(su + f * sfield, gu + f * gfield);
+                else if (PL::CHUNK == 8) cp_async_8(su + f * sfield, gu + f * gfield);
+                else cp_async_4(su + f * sfield, gu + f * gfield);
+                if (gd) {
+                    if (PL::CHUNK == 16) cp_async_16(sd + f * sfield, gd + f * gfield);
+                    else if (PL::CHUNK == 8) cp_async_8(sd + f * sfield, gd + f * gfield);
+                    else cp_async_4(sd + f * sfield, gd + f * gfield);
+                }
             }
         }
         cp_async_commit();
