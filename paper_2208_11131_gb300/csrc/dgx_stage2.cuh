@@ -363,14 +363,29 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
             cp_async_wait_all();
             __syncthreads();
         } else {
-            // synchronous load of u^n (+ delta) of tile and halo into sU
-            for (int idx = tid; idx < NF * NSLOT * NP; idx += nth) {
-                const int l = idx % NP;
-                const int fs = idx / NP;
-                const int g = sG[fs % NSLOT];
+            // synchronous load of u^n (+ delta) of tile and halo into sU: one (slot, chunk) pair per
+            // thread and pass, chunks of the widest aligned width, all fields by a constant stride
+            constexpr int E = PL::CHUNK / (int)sizeof(Real);  // values per chunk
+            constexpr int PER = PL::CELL_BYTES / PL::CHUNK;
+            for (int p = tid; p < NSLOT * PER; p += nth) {
+                const int slot = p / PER, c = p % PER;
+                const int g = sG[slot];
                 if (g < 0) continue;
-                const size_t gi = ((size_t)(fs / NSLOT) * A.ncell + g) * NP + l;
-                sU[fs * NPS + l] = ub[gi] + (di ? dsc * di[gi] : Real(0));
+                const size_t g0 = (size_t)g * NP + (size_t)c * E;
+                Real *dst = sU + slot * NPS + c * E;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    const size_t gi = g0 + (size_t)f * A.ncell * NP;
+                    Real v[E];
+                    ld_line<E, PL::CHUNK>(ub + gi, v);
+                    if (di) {
+                        Real dd[E];
+                        ld_line<E, PL::CHUNK>(di + gi, dd);
+#pragma unroll
+                        for (int e = 0; e < E; ++e) v[e] = v[e] + dsc * dd[e];
+                    }
+                    st_line<E, PL::CHUNK>(dst + f * NSLOT * NPS, v);
+                }
             }
             __syncthreads();
         }
