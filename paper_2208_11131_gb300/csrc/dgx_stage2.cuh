@@ -846,6 +846,16 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                 const int g = sG[c];
                 if (g < 0) continue;
                 const int base = fc * NPS + r * Q;
+                const size_t gi = ((size_t)f * A.ncell + g) * NP + (size_t)r * Q;
+                // library-owned arrays: a line starts at a multiple of Q values, so the widest
+                // aligned access of the line's bytes is legal
+                constexpr int VD = (Q * 8) % 16 == 0 ? 16 : 8;
+                constexpr int VF = (Q * 4) % 16 == 0 ? 16 : ((Q * 4) % 8 == 0 ? 8 : 4);
+                // u^n of the line is loaded before the transposed pass: the compiler may not move
+                // the load past the earlier stores it cannot prove disjoint, and this way its latency
+                // overlaps the arithmetic
+                double uo[Q];
+                if (A.mode == 2) ld_line<Q, VD>(A.uold + gi, uo);
                 Real w[Q], L[Q];
                 ld_line<Q, VEC>(sR + base, w);
 #pragma unroll
@@ -855,7 +865,6 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                     for (int i = 0; i < Q; ++i) acc = fma(Tg.B[i][l], w[i], acc);
                     L[l] = acc;
                 }
-                const size_t gi = ((size_t)f * A.ncell + g) * NP + (size_t)r * Q;
                 if (A.total_degree) {
                     // total-degree basis: modes with l_x + l_y + l_z > n are not in the space and stay 0
                     const int lyz = r % Q + (DIM == 3 ? r / Q : 0);
@@ -868,10 +877,6 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                     for (int l = 0; l < Q; ++l) A.rhs_out[gi + l] = (double)L[l];
                     continue;
                 }
-                // library-owned arrays: a line starts at a multiple of Q values, so the widest
-                // aligned access of the line's bytes is legal
-                constexpr int VD = (Q * 8) % 16 == 0 ? 16 : 8;
-                constexpr int VF = (Q * 4) % 16 == 0 ? 16 : ((Q * 4) % 8 == 0 ? 8 : 4);
                 Real din[Q], xv[Q], dnew[Q], zn[Q];
                 if (di) {
                     ld_line<Q, VEC>(di + gi, din);
@@ -897,8 +902,7 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                 if (A.mode == 1) {
                     st_line<Q, VEC>(dout + gi, dnew);
                 } else {
-                    double uo[Q], un[Q];
-                    ld_line<Q, VD>(A.uold + gi, uo);
+                    double un[Q];
 #pragma unroll
                     for (int l = 0; l < Q; ++l) un[l] = uo[l] + (double)dnew[l];
                     st_line<Q, VD>(A.unew + gi, un);
