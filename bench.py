@@ -36,7 +36,8 @@ if ROOT not in sys.path:
 METRIC = "DOF-updates/s per GB300 (FP32-bulk vs FP64, same L1 error) + % HBM roofline"
 UNIT = "DOF-updates/s"
 FLUSH_BYTES = 256 << 20
-KERNEL_SRCS = [os.path.join(ROOT, "paper_2208_11131_gb300", "csrc", f) for f in ("dgx_kernels.cuh", "dgx_stage2.cuh")]
+KERNEL_SRCS = [os.path.join(ROOT, "paper_2208_11131_gb300", "csrc", f)
+               for f in ("dgx_kernels.cuh", "dgx_stage2.cuh", "dgx_inst.cuh", "dgx_inst_2d_f32.cu", "dgx_inst_3d_f32.cu")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
 
 
@@ -152,7 +153,8 @@ def measured_peaks():
 
 
 def kernel_sha() -> str:
-    """sha256 over the stage kernel's sources (a traffic figure is only used for the kernel it was taken on)"""
+    """sha256 over the stage kernel's sources and the FP32 tile tables (a traffic figure is only used for
+    the kernel and tiles it was taken on)"""
     h = hashlib.sha256()
     for f in KERNEL_SRCS:
         h.update(open(f, "rb").read())

@@ -363,28 +363,40 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
             cp_async_wait_all();
             __syncthreads();
         } else {
-            // synchronous load of u^n (+ delta) of tile and halo into sU: one (slot, chunk) pair per
-            // thread and pass, chunks of the widest aligned width, all fields by a constant stride
-            constexpr int E = PL::CHUNK / (int)sizeof(Real);  // values per chunk
-            constexpr int PER = PL::CELL_BYTES / PL::CHUNK;
-            for (int p = tid; p < NSLOT * PER; p += nth) {
-                const int slot = p / PER, c = p % PER;
+            // synchronous load of u^n (+ delta) of tile and halo fused with pass A (x-lines, modal ->
+            // nodal): one (slot, x-line) per thread and pass, all fields by a constant stride so that
+            // their loads are in flight together, transformed in registers and stored as nodal values;
+            // the modal density of the tile's own cells is kept in sR (free until the volume phase) for
+            // the sensor of the fused first stage
+            constexpr int LPC = NP / Q;  // x-lines per cell
+            const bool keep = AV && A.fused;
+            for (int p = tid; p < NSLOT * LPC; p += nth) {
+                const int slot = p / LPC, r = p % LPC;
                 const int g = sG[slot];
                 if (g < 0) continue;
-                const size_t g0 = (size_t)g * NP + (size_t)c * E;
-                Real *dst = sU + slot * NPS + c * E;
+                // library-owned arrays: a line starts at a multiple of Q values, so VEC accesses are legal
+                const size_t g0 = (size_t)g * NP + (size_t)r * Q;
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
                     const size_t gi = g0 + (size_t)f * A.ncell * NP;
-                    Real v[E];
-                    ld_line<E, PL::CHUNK>(ub + gi, v);
+                    Real w[Q];
+                    ld_line<Q, VEC>(ub + gi, w);
                     if (di) {
-                        Real dd[E];
-                        ld_line<E, PL::CHUNK>(di + gi, dd);
+                        Real dd[Q];
+                        ld_line<Q, VEC>(di + gi, dd);
 #pragma unroll
-                        for (int e = 0; e < E; ++e) v[e] = v[e] + dsc * dd[e];
+                        for (int m = 0; m < Q; ++m) w[m] = w[m] + dsc * dd[m];
                     }
-                    st_line<E, PL::CHUNK>(dst + f * NSLOT * NPS, v);
+                    if (f == 0 && keep && slot < TC) st_line<Q, VEC>(sR + slot * NPS + r * Q, w);
+                    Real o[Q];
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) {
+                        Real acc = Real(0);
+#pragma unroll
+                        for (int m = 0; m < Q; ++m) acc = fma(Tg.B[i][m], w[m], acc);
+                        o[i] = acc;
+                    }
+                    st_line<Q, VEC>(sU + (f * NSLOT + slot) * NPS + r * Q, o);
                 }
             }
             __syncthreads();
@@ -430,17 +442,15 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                 sWig[c] = (Real)wg;
             }
         };
-        if constexpr (!PF) {
-            if (AV) {
-                cell_wiggle(sU);
-                __syncthreads();
-            }
-        } else if (AV) {
-            cell_wiggle(sIn0);  // the modal u^n stays in sIn0 during pass A (first stage: no delta)
+        // (the barrier after pass B orders these reads and the sWig writes before the volume phase)
+        if (AV) {
+            if constexpr (PF) cell_wiggle(sIn0);  // the modal u^n stays in sIn0 during pass A (first stage: no delta)
+            else cell_wiggle(sR);
         }
 
-        // ---- pass A: x-lines, modal -> nodal, from the loaded input (u^n + delta)
-        {
+        // ---- pass A: x-lines, modal -> nodal, from the loaded input (u^n + delta); without prefetch
+        // buffers it is part of the load above
+        if constexpr (PF) {
             constexpr int LINES = NF * NSLOT * (NP / Q);
             for (int idx = tid; idx < LINES; idx += nth) {
                 const int fs = idx / (NP / Q);
@@ -448,16 +458,12 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                 if (sG[fs % NSLOT] < 0) continue;
                 const int base = fs * NPS + r * Q;
                 Real w[Q];
-                if constexpr (PF) {
-                    ld_line<Q, VEC>(sIn0 + base, w);
-                    if (di) {
-                        Real dd[Q];
-                        ld_line<Q, VEC>(sIn1 + base, dd);
+                ld_line<Q, VEC>(sIn0 + base, w);
+                if (di) {
+                    Real dd[Q];
+                    ld_line<Q, VEC>(sIn1 + base, dd);
 #pragma unroll
-                        for (int m = 0; m < Q; ++m) w[m] = fma(dsc, dd[m], w[m]);
-                    }
-                } else {
-                    ld_line<Q, VEC>(sU + base, w);
+                    for (int m = 0; m < Q; ++m) w[m] = fma(dsc, dd[m], w[m]);
                 }
                 Real o[Q];
 #pragma unroll
@@ -469,8 +475,8 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                 }
                 st_line<Q, VEC>(sU + base, o);
             }
+            __syncthreads();
         }
-        __syncthreads();
         // the input buffers are free: start streaming the next tile
         const int next = tile + gridDim.x;
         if (PF && next < ntiles) {
