@@ -1004,6 +1004,9 @@ constexpr bool stage2_prefetch()
     using P1 = Stage2Plan<DIM, N, Real, AV, NSM, TX, TY, TZ, true>;
     using P0 = Stage2Plan<DIM, N, Real, AV, NSM, TX, TY, TZ, false>;
     constexpr size_t sm = 228 * 1024, reserve = 1024;  // shared memory per SM, reserved per CTA
+    // 2-D FP32 (two CTAs per SM): the synchronous load fused with pass A measured faster than the
+    // prefetch buffers at every degree, one CTA's load overlapping the other's arithmetic
+    if (DIM == 2 && sizeof(Real) == 4) return false;
     if (P1::BYTES > 227 * 1024) return false;
     return P1::MINB * (P1::BYTES + reserve) <= sm || P0::MINB * (P0::BYTES + reserve) > sm;
 }
@@ -1011,8 +1014,9 @@ constexpr bool stage2_prefetch()
 template <int DIM, int N, typename Real, bool AV, int NSM, int TX, int TY, int TZ>
 cudaError_t run_stage2(const StageArgs &a, const Tables<Real> &t, cudaStream_t s, int *grid_out)
 {
-    // prefetch buffers when the tile still fits in shared memory with them, as many times per SM
-    // as the registers are bounded for (else the resident CTAs, not the prefetch, hide latency)
+    // prefetch buffers (not for 2-D FP32) when the tile still fits in shared memory with them, as
+    // many times per SM as the registers are bounded for (else the resident CTAs, not the prefetch,
+    // hide latency)
     constexpr bool PF = stage2_prefetch<DIM, N, Real, AV, NSM, TX, TY, TZ>();
     using PL = Stage2Plan<DIM, N, Real, AV, NSM, TX, TY, TZ, PF>;
     auto k = stage2_kernel<DIM, N, Real, AV, NSM, TX, TY, TZ, PF>;
