@@ -23,6 +23,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -157,8 +158,16 @@ def kernel_sha() -> str:
     the kernel and tiles it was taken on)"""
     h = hashlib.sha256()
     for f in KERNEL_SRCS:
-        h.update(open(f, "rb").read())
+        h.update(code_only(open(f).read()).encode())
     return h.hexdigest()
+
+
+def code_only(src: str) -> str:
+    """C++ source without comments and with whitespace runs collapsed (edits of comments alone do
+    not change the kernel)"""
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return " ".join(src.split())
 
 
 def traffic_for(key: str):

@@ -2,9 +2,11 @@
 //
 // Same arithmetic as stage_kernel (collocated rewriting of the modal sums of
 // Eq. time_stepping_final, see dgx_kernels.cuh); different organisation for sm_103a:
-//  * one CTA loops over tiles; while it works on tile k the state of tile k+1 (u^n and delta,
-//    tile + halo) streams into shared memory with cp.async, so global-load latency is hidden
-//    behind the compute of the current tile;
+//  * one CTA loops over tiles. Plans with prefetch buffers stream the state of tile k+1 (u^n and
+//    delta, tile + halo) into shared memory with cp.async while the CTA works on tile k; plans
+//    without them (2-D FP32, two resident CTAs per SM) load a tile synchronously, straight into
+//    registers, with the first modal->nodal pass applied before the only shared-memory store,
+//    and rely on the other resident CTA to cover the load latency;
 //  * the field count and the Navier-Stokes / artificial-viscosity switches are template
 //    parameters, so every field loop unrolls;
 //  * the modal<->nodal transforms work on whole lines of n+1 values: a thread reads its line
@@ -276,7 +278,7 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
         const Real *di = static_cast<const Real *>(T.din);
         for (int s = tid; s < NSLOT; s += nth) sG[s] = slot_global<S>(s, o, V, T.N, T.bc);
         __syncthreads();
-        if constexpr (!PF) return;  // without prefetch buffers the tile is loaded at the top of its iteration
+        if constexpr (!PF) return;  // without prefetch buffers the tile is loaded (fused with pass A) at the top of its iteration
         constexpr int PER = PL::CELL_BYTES / PL::CHUNK;  // chunks per (field, cell)
         // one (slot, chunk) pair per thread and pass, all fields by a constant stride
         const size_t gfield = (size_t)T.ncell * NP * sizeof(Real);          // bytes between fields
