@@ -199,13 +199,22 @@ def barrier(ws):
 
 
 def allreduce_max(x, ws):
+    """the maximum of x over the ranks (a device tensor under NCCL, a host one under gloo)"""
     if ws <= 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(local_ms, units_per_rank, ws):
+    """whole-job throughput of ws replicas: the units all ranks processed over the slowest rank's
+    time; returns (that time in ms, units per second)"""
+    total_ms = allreduce_max(local_ms, ws)
+    return total_ms, units_per_rank * ws / (total_ms / 1e3)
 
 
 def l1_error_of(wl, w, func):
@@ -420,9 +429,7 @@ def dgx_arm(args, rank, ws, local):
     clk = clocks.stop()
     sim.sync()
     step_ms = [sum(x) for x in per_launch]
-    total_ms = allreduce_max(sum(step_ms), ws)
-    units = wl.dofs * 5 * args.steps * ws
-    value = units / (total_ms / 1e3)
+    total_ms, value = job_value(sum(step_ms), wl.dofs * 5 * args.steps, ws)
     stage_ms = sum(sum(x[2:]) for x in per_launch)
     launches = args.steps * 5
     bpv = stage_bytes_per_value(fp32)
