@@ -77,6 +77,42 @@ def test_rhs_parity(dim, n, N, box, bc, nu, av, prec):
     sim.close()
 
 
+DEGENERATE_CASES = [
+    # one cell along an axis: the cell is its own periodic neighbour, or both its faces are outflow
+    # boundaries; a single periodic cell
+    (2, 3, (1, 5), (1.0, 0.7), (1, 0)),
+    (2, 2, (7, 1), (1.0, 0.7), (0, 0)),
+    (2, 3, (1, 1), (1.0, 0.7), (0, 0)),
+    (2, 1, (1, 4), (1.0, 0.7), (1, 0)),
+    (3, 2, (1, 2, 3), (1.0, 0.7, 0.9), (0, 0, 0)),
+    (3, 1, (2, 1, 1), (1.0, 0.7, 0.9), (0, 1, 0)),
+]
+
+
+@pytest.mark.parametrize("dim,n,N,box,bc", DEGENERATE_CASES)
+@pytest.mark.parametrize("prec", [dgx.DG_FP64, dgx.DG_FP32_BULK])
+def test_rhs_parity_degenerate_grids(dim, n, N, box, bc, prec):
+    wl = _wl(dim, n, N, box, bc, 1e-3, 1)
+    w = inputs.random_modal_state(wl, seed=7 + n)
+    ref, st = oracle.rhs(problem(wl), w)
+    assert st == 0
+    sim = dgx.Simulation(wl, precision=prec)
+    sim.set_state(w)
+    out = sim.rhs()
+    err = rhs_err(out, ref, problem(wl), w)
+    assert err < (FP64_RHS_TOL if prec == dgx.DG_FP64 else FP32_RHS_TOL), err
+    # a whole step
+    o = oracle.Sim(problem(wl), w)
+    _, st = o.step()
+    assert st == 0
+    sim.step()
+    if prec == dgx.DG_FP64:
+        assert state_err(sim.get_state(), o.w, problem(wl)) < 1e-11
+    else:
+        assert rel_l1(sim.get_state(), o.w, 0) < 1e-5
+    sim.close()
+
+
 def _run_both(wl, w0, nsteps, prec, dt=0.0, rk=0):
     P = problem(wl, rk_stages=rk)
     ref = oracle.Sim(P, w0)
