@@ -393,11 +393,11 @@ int alloc_buffers(dg_t *h)
     if (!st) st = al((void **)&h->dtp, 4 * sizeof(double));
     int pt[3], sdummy[3];
     if (h->dim == 2) {
-        if (fp32(h)) tiles_2d_f32(h->degree, sdummy, pt);
-        else tiles_2d_f64(h->degree, sdummy, pt);
+        if (fp32(h)) tiles_2d_f32(h->degree, h->p.tracer_on, sdummy, pt);
+        else tiles_2d_f64(h->degree, h->p.tracer_on, sdummy, pt);
     } else {
-        if (fp32(h)) tiles_3d_f32(h->degree, sdummy, pt);
-        else tiles_3d_f64(h->degree, sdummy, pt);
+        if (fp32(h)) tiles_3d_f32(h->degree, h->p.tracer_on, sdummy, pt);
+        else tiles_3d_f64(h->degree, h->p.tracer_on, sdummy, pt);
     }
     for (int a = 0; a < 3; ++a) {
         h->stile[a] = sdummy[a];

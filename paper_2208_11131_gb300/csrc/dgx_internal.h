@@ -239,9 +239,10 @@ cudaError_t launch_forcing_eval_f64(int dim, int degree, const int *N, long long
 cudaError_t launch_forcing_eval_f32(int dim, int degree, const int *N, long long ncell, const float *tab,
                                     const long long *off, const double *smodes, float *out, cudaStream_t s);
 
-void tiles_2d_f64(int degree, int *stage, int *pro);
-void tiles_2d_f32(int degree, int *stage, int *pro);
-void tiles_3d_f64(int degree, int *stage, int *pro);
-void tiles_3d_f32(int degree, int *stage, int *pro);
+// stage and prologue tiles of a degree (tracer != 0: the stage tiles of the plans with a tracer)
+void tiles_2d_f64(int degree, int tracer, int *stage, int *pro);
+void tiles_2d_f32(int degree, int tracer, int *stage, int *pro);
+void tiles_3d_f64(int degree, int tracer, int *stage, int *pro);
+void tiles_3d_f32(int degree, int tracer, int *stage, int *pro);
 
 }  // namespace dgx

@@ -1085,20 +1085,24 @@ cudaError_t run_stage2_batch_any(int av, int ns, const StageArgs *descs, const i
     return run_stage2_batch<DIM, N, Real, false, 0, TX, TY, TZ>(descs, tile_off, nsims, total_tiles, t, s);
 }
 
-// run-time (AV, diffusion mode) dispatch onto the compile-time variants; a tracer always takes the
-// diffusive path (its eta, nu and kappa may be zero)
-template <int DIM, int N, typename Real, int TX, int TY, int TZ>
+// run-time (AV, diffusion mode) dispatch onto the compile-time variants.  The tracer plans (TRACER)
+// have a tile table of their own (their sixth field takes more shared memory) and always take the
+// diffusive path (eta, nu and kappa may be zero); the others are Euler or Navier-Stokes.
+template <int DIM, int N, typename Real, int TX, int TY, int TZ, bool TRACER>
 cudaError_t run_stage2_any(const StageArgs &a, const Tables<Real> &t, cudaStream_t s, int *grid)
 {
-    const int m = a.tracer_on ? 2 : (a.ns_on ? 1 : 0);
-    if (a.av_on) {
-        if (m == 2) return run_stage2<DIM, N, Real, true, 2, TX, TY, TZ>(a, t, s, grid);
-        if (m == 1) return run_stage2<DIM, N, Real, true, 1, TX, TY, TZ>(a, t, s, grid);
-        return run_stage2<DIM, N, Real, true, 0, TX, TY, TZ>(a, t, s, grid);
+    if (!a.tracer_on != !TRACER) return cudaErrorInvalidValue;
+    if constexpr (TRACER) {
+        if (a.av_on) return run_stage2<DIM, N, Real, true, 2, TX, TY, TZ>(a, t, s, grid);
+        return run_stage2<DIM, N, Real, false, 2, TX, TY, TZ>(a, t, s, grid);
+    } else {
+        if (a.av_on) {
+            if (a.ns_on) return run_stage2<DIM, N, Real, true, 1, TX, TY, TZ>(a, t, s, grid);
+            return run_stage2<DIM, N, Real, true, 0, TX, TY, TZ>(a, t, s, grid);
+        }
+        if (a.ns_on) return run_stage2<DIM, N, Real, false, 1, TX, TY, TZ>(a, t, s, grid);
+        return run_stage2<DIM, N, Real, false, 0, TX, TY, TZ>(a, t, s, grid);
     }
-    if (m == 2) return run_stage2<DIM, N, Real, false, 2, TX, TY, TZ>(a, t, s, grid);
-    if (m == 1) return run_stage2<DIM, N, Real, false, 1, TX, TY, TZ>(a, t, s, grid);
-    return run_stage2<DIM, N, Real, false, 0, TX, TY, TZ>(a, t, s, grid);
 }
 
 }  // namespace dgx

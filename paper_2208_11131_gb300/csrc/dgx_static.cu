@@ -96,9 +96,9 @@ extern "C" int dg_max_dt_noalloc(const dg_grid *grid, int degree, double gamma, 
     if (ncell > 0x7fffffffLL) return DG_EINVAL;
     int st[3], pt[3];
     if (grid->dim == 2)
-        tiles_2d_f64(degree, st, pt);
+        tiles_2d_f64(degree, 0, st, pt);
     else
-        tiles_3d_f64(degree, st, pt);
+        tiles_3d_f64(degree, 0, st, pt);
     PrologueArgs a{};
     long long nblk = 1;
     for (int i = 0; i < 3; ++i) {
