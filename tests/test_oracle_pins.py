@@ -478,3 +478,38 @@ def test_periodic_degenerate_grids_conserve(dim, n, N):
     u[dim + 1, :, 0] = 1.0 / 0.4 + 0.5 * 1.1 * v @ v
     r0, st = oracle.rhs(P, u)
     assert st == 0 and np.abs(r0[:dim + 2]).max() < 1e-13
+
+
+def test_wiggle_source_closed_form():
+    """Sec. 4.1 wiggle term of the alpha source, one value per cell per step: f_w max(0, d ln S / dt)
+    where the sensor S exceeds s_onset / P^2, else 0, with d ln S / dt the difference of ln S between
+    the starts of this and the previous step over the previous step's dt (S floored at
+    1e-4 s_onset / P^2), and zero at the first step.  Each cell carries one top density mode of
+    amplitude a on a unit mean, so S = a^2 / (1 + a^2) exactly."""
+    n, g = 3, 1.4
+    P = n + 1
+    prob = oracle.Problem(dim=2, n=n, N=(7, 1), gamma=g, av_on=1)
+    s_on = prob.s_onset / P**2
+    floor = 1e-4 * s_on
+    # above the onset and growing / shrinking; growing below the onset; a floored history; below the
+    # floor; unchanged; between s_onset / P^2 and s_onset (on only with the 1 / P^2)
+    a = np.array([0.1, 0.1, 1e-3, 0.02, 1e-6, 0.05, 0.005])
+    S = a**2 / (1 + a**2)
+    assert s_on < S[6] < prob.s_onset
+    S_prev = np.array([S[0] / 2, 2 * S[1], S[2] / 10, 1e-14, 1e-20, S[5], S[6] / 3])
+    w = np.zeros(prob.shape())
+    w[0, :, 0] = 1.0
+    w[0, :, n] = a  # mode (l_x, l_y) = (n, 0)
+    w[3, :, 0] = 1.0 / (g - 1)  # at rest, p = 1
+    dt_prev = 0.01
+    expect = np.where(S > s_on, prob.f_w * np.maximum(0.0, (np.log(np.maximum(S, floor)) -
+                                                           np.log(np.maximum(S_prev, floor))) / dt_prev), 0.0)
+    assert expect[0] > 0 and expect[3] > 0 and expect[6] > 0 and not np.any(expect[[1, 2, 4, 5]])
+    sim = oracle.Sim(prob, w, S_prev=S_prev.copy(), scal=np.array([dt_prev, 1.0, 0.0]))
+    _, st = sim.step(1e-9)
+    assert st == 0
+    assert np.allclose(sim.wig, expect, rtol=1e-12, atol=0.0)
+    assert np.allclose(sim.S_prev, S, rtol=1e-13, atol=0.0)  # the history now holds this step's sensor
+    first = oracle.Sim(prob, w, S_prev=S_prev.copy(), scal=np.array([0.0, 0.0, 0.0]))
+    _, st = first.step(1e-9)
+    assert st == 0 and not np.any(first.wig)
