@@ -284,6 +284,36 @@ def reference_arm(args, rank, ws):
     print(json.dumps(line), flush=True)
 
 
+def step_working_set_bytes(nvals: int, fp32: bool) -> int:
+    """bytes of the state arrays one SSP(5,4) step touches: u^n and u^{n+1} (FP64), in the bulk mode
+    their FP32 copies, and the three delta registers (stage precision)"""
+    return nvals * ((8 + 8 + 4 + 4 + 3 * 4) if fp32 else (8 + 8 + 3 * 8))
+
+
+def stage_roofline(nvals: int, ncell: int, fp32: bool, stage_ms: float, peak_gbs: float) -> dict:
+    """HBM roofline of the stage launches of one SSP(5,4) step: algorithmic bytes (every array a stage
+    reads once and writes once, plus the per-cell wiggle source) over the summed stage-launch time"""
+    nbytes = nvals * sum(stage_bytes_per_value(fp32)) + 5 * 8 * ncell
+    achieved = nbytes / (stage_ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s", "frac": achieved / peak_gbs,
+            "algorithmic_bytes_per_launch": nbytes / 5, "avg_launch_ms": stage_ms / 5}
+
+
+def l2_bytes(device: int):
+    """the device's L2 size in bytes, or None where the runtime does not report it"""
+    try:
+        import torch
+        return int(getattr(torch.cuda.get_device_properties(device), "L2_cache_size"))
+    except Exception:
+        return None
+
+
+def l2_resident(working_set: int, device: int):
+    """whether a step's working set fits in L2 (None if the L2 size is unknown)"""
+    l2 = l2_bytes(device)
+    return None if l2 is None else working_set <= l2
+
+
 def rk_stages_for(n: int) -> int:
     """default SSP-RK stage count of degree n (the library's choice when rk_stages is 0)"""
     return {0: 1, 1: 2, 2: 3}.get(n, 5)
@@ -352,13 +382,24 @@ def side_workloads(dgx, inputs, oracle_l1, torch, stream, flush):
         sim.set_state(w0)
         for _ in range(warm):
             dgx.dg_step_timed(sim.h, 0.0, 7)
-        ms = []
+        ms, stage_ms = [], []
         for k in range(steps):
             flush.fill_(k & 0xFF)
-            ms.append(sum(dgx.dg_step_timed(sim.h, 0.0, 7)))
+            t = dgx.dg_step_timed(sim.h, 0.0, 7)
+            ms.append(sum(t))
+            stage_ms.append(sum(t[2:]))  # the stage launches (slots 0, 1: driving, prologue)
         sim.close()
         m = float(np.mean(ms))
-        return {"ms_per_step": m, "value": wl.dofs * stages / (m / 1e3), "unit": UNIT, "steps": steps}
+        out = {"ms_per_step": m, "value": wl.dofs * stages / (m / 1e3), "unit": UNIT, "steps": steps}
+        if stages == 5:
+            try:
+                peak = float(measured_peaks()[0]["hbm_gbs"])
+                out["roofline"] = stage_roofline(wl.nfields * wl.ncell * wl.M, wl.ncell, True,
+                                                 float(np.mean(stage_ms)), peak)
+                out["working_set_bytes"] = step_working_set_bytes(wl.nfields * wl.ncell * wl.M, True)
+            except Exception as e:  # a side figure never costs the benchmark line
+                out["roofline_error"] = repr(e)
+        return out
 
     wl = inputs.c2_shear_layer(N=256, n=3).with_(tracer_on=1, eta=1e-5)
     w = inputs.project(wl.with_(tracer_on=0), inputs.shear_layer_ic(wl.with_(tracer_on=0)))
@@ -450,7 +491,10 @@ def dgx_arm(args, rank, ws, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64", "data": "synthetic",
             "config": config_of(wl, label=label,
                                 extra={"precision": "fp32-bulk (fp64 state and RK accumulation)" if fp32 else "fp64",
-                                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"}),
+                                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                                       "working_set_bytes": step_working_set_bytes(nvals, fp32),
+                                       "l2_bytes": l2_bytes(local),
+                                       "l2_resident": l2_resident(step_working_set_bytes(nvals, fp32), local)}),
             "roofline": roof, "clocks": clk,
             # launches the library made per step: folded-away slots of dg_step_timed read 0
             "gpu_launches": args.steps * sum(1 for i in range(nl) if np.mean([x[i] for x in per_launch]) > 0),

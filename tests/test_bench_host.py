@@ -33,3 +33,23 @@ def test_traffic_lookup_follows_the_kernel_hash(tmp_path, monkeypatch):
     assert bench.traffic_for("stage_kernel|w|fp32") is None
     assert bench.traffic_for("stage_kernel|other|fp32") is None
 
+
+
+def test_stage_roofline_matches_the_headline_bytes():
+    # the 256^2 degree-3 shear layer: 5 fields x 65,536 cells x 16 modes
+    nvals, ncell = 5 * 65536 * 16, 65536
+    r = bench.stage_roofline(nvals, ncell, True, stage_ms=0.4, peak_gbs=6786.2)
+    assert r["algorithmic_bytes_per_launch"] == 88604672.0  # the figure the benchmark line reports
+    assert abs(r["achieved"] - 5 * 88604672.0 / 0.4e-3 / 1e9) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / 6786.2) < 1e-15 and r["avg_launch_ms"] == 0.08
+    assert sum(bench.stage_bytes_per_value(True)) == 84 and sum(bench.stage_bytes_per_value(False)) == 136
+
+
+def test_working_set_and_l2_flag():
+    nvals = 5 * 65536 * 16
+    assert bench.step_working_set_bytes(nvals, True) == 36 * nvals  # 189 MB: above the 129 MB L2
+    assert bench.step_working_set_bytes(nvals, False) == 40 * nvals  # u^n, u^{n+1}, three deltas
+    if bench.l2_bytes(0) is None:  # no device here
+        assert bench.l2_resident(1, 0) is None
+    else:
+        assert bench.l2_resident(1, 0) is True
