@@ -513,3 +513,32 @@ def test_wiggle_source_closed_form():
     first = oracle.Sim(prob, w, S_prev=S_prev.copy(), scal=np.array([0.0, 0.0, 0.0]))
     _, st = first.step(1e-9)
     assert st == 0 and not np.any(first.wig)
+
+
+def test_artificial_viscosity_diffuses_a_density_wave_at_rest():
+    """Sec. 4.1 artificial viscosity alone: gas at rest at uniform pressure carrying a small density
+    sine along x, with alpha = 1.  Every face sees a stationary contact, which HLLC returns exactly
+    (no mass or energy flux, the same pressure on both sides), so the only flux is eps grad u with
+    eps = av_scale clip(alpha, 0, 1) c_s h / P, h = min_a h_a (here h_x: the cells are twice as tall
+    as wide).  The cell-mean density right-hand side is then eps_0 times the cell average of rho''
+    (up to O(delta) from the variation of c_s and the recovery error, which falls with h), and
+    momentum and energy do not change."""
+    g, delta, n = 1.4, 1e-5, 3
+    errs = []
+    for N in (8, 16, 32):
+        P = oracle.Problem(dim=2, n=n, N=(N, N), hi=(1.0, 2.0), gamma=g, av_on=1)
+
+        def ic(X):
+            one = np.ones(len(X))
+            return np.stack([1 + delta * np.sin(2 * np.pi * X[:, 0]), 0 * one, 0 * one, one / (g - 1), one])
+        w = oracle.project(P, ic)
+        r, st = oracle.rhs(P, w)
+        assert st == 0
+        h = 1.0 / N
+        eps0 = P.av_scale * np.sqrt(g) * h / (n + 1)  # c_s = sqrt(gamma p / rho) = sqrt(gamma)
+        xc = P.cell_centres()[:, 0]
+        avg_rho2 = -(2 * np.pi) * delta * (np.cos(2 * np.pi * (xc - h / 2)) - np.cos(2 * np.pi * (xc + h / 2))) / h
+        expect = eps0 * avg_rho2
+        errs.append(np.abs(r[0, :, 0] - expect).max() / np.abs(expect).max())
+        assert np.abs(r[1:4]).max() < 1e-12
+    assert errs[1] < 1e-4 and errs[2] < errs[1] / 4 and errs[1] < errs[0] / 4, errs
