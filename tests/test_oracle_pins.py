@@ -568,3 +568,29 @@ def test_alpha_compression_source():
         expect = (src * wg[None, :]).sum(1) / 2.0  # the field is constant in y: the y-rule sums to 2
         errs.append(np.abs(r[4, :, 0] - expect).max() / np.abs(expect).max())
     assert errs[1] < 1e-5 and errs[2] < errs[1] / 8 and errs[1] < errs[0] / 8, errs
+
+
+def test_outflow_faces_carry_the_physical_flux_of_the_interior_trace():
+    """Outflow boundaries (the reading of the design notes: the ghost trace is the interior trace, so
+    the face flux is the physical Euler flux of the interior trace and no dissipative flux crosses the
+    boundary).  One cell with outflow at both x faces, varying in x only, Navier-Stokes on: the cell
+    mean changes by -(F(u(+1)) - F(u(-1))) / h_x with u(+-1) the cell's own traces (the y faces are
+    periodic onto the cell itself and cancel; the volume terms do not reach the cell mean)."""
+    g, n, hx = 1.4, 2, 0.5
+    P = oracle.Problem(dim=2, n=n, N=(1, 1), hi=(hx, 0.7), bc=(1, 0), gamma=g, nu=1e-2, kappa=1e-2, av_on=0)
+    w = np.zeros(P.shape())
+    w[0, 0, :3] = (1.0, 0.1, 0.05)  # modes l_x = 0, 1, 2 with l_y = 0
+    w[1, 0, :2] = (0.3, 0.05)
+    w[2, 0, 0] = 0.1
+    w[3, 0, :2] = (2.5, 0.1)
+    r, st = oracle.rhs(P, w)
+    assert st == 0
+
+    def flux(x):
+        u = np.array([sum(w[f, 0, l] * oracle.pt(l, x) for l in range(n + 1)) for f in range(4)])
+        rho, mx, my, e = u
+        vx, vy = mx / rho, my / rho
+        p = (g - 1) * (e - 0.5 * rho * (vx * vx + vy * vy))
+        return np.array([mx, mx * vx + p, mx * vy, (e + p) * vx])
+    expect = -(flux(1.0) - flux(-1.0)) / hx
+    assert np.allclose(r[:4, 0, 0], expect, rtol=1e-13, atol=1e-13), (r[:4, 0, 0], expect)
