@@ -109,7 +109,8 @@ def test_gaussian_pulse_per_step_parity():
 @pytest.mark.parametrize("prec", [dgx.DG_FP64, dgx.DG_FP32_BULK])
 @pytest.mark.parametrize("n,lo,hi", [(1, 1.7, 2.5), (2, 1.8, 2.5), (3, 3.7, 4.6)])
 def test_gaussian_pulse_convergence(n, lo, hi, prec):
-    """the orders the oracle gives (design notes: order 2 at n = 2 with the paper's f = 3/4)"""
+    """the orders the oracle gives (order 2 at n = 2: the recovery of Sec. 3.2 with the paper's overlap
+    fraction f = 3/4 gives 2 there, f = 1 would give 3)"""
     errs = []
     for N in (16, 32):
         wl = inputs.gaussian_pulse(N=N, n=n)

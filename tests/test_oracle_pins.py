@@ -571,9 +571,9 @@ def test_alpha_compression_source():
 
 
 def test_outflow_faces_carry_the_physical_flux_of_the_interior_trace():
-    """Outflow boundaries (the reading of the design notes: the ghost trace is the interior trace, so
-    the face flux is the physical Euler flux of the interior trace and no dissipative flux crosses the
-    boundary).  One cell with outflow at both x faces, varying in x only, Navier-Stokes on: the cell
+    """Outflow boundaries (the reading taken where the paper is silent: the ghost trace is the
+    interior trace, so the face flux is the physical Euler flux of the interior trace and no
+    dissipative flux crosses the boundary).  One cell with outflow at both x faces, varying in x only, Navier-Stokes on: the cell
     mean changes by -(F(u(+1)) - F(u(-1))) / h_x with u(+-1) the cell's own traces (the y faces are
     periodic onto the cell itself and cancel; the volume terms do not reach the cell mean)."""
     g, n, hx = 1.4, 2, 0.5

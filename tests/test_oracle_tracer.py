@@ -7,7 +7,8 @@ contact), the flow fields are untouched by the tracer bit for bit, tracer conser
 advection of a smooth concentration, and the convergence of the diffusing Gaussian pulse against
 its closed form.  The last pins the recovered gradients of Sec. 3.2: with the paper's overlap
 fraction (f = 3/4 for n <= 2, f = 1 above) the pulse converges at order 2 for n = 1, 4 for n = 3,
-and 2 (not 3) for n = 2 -- see the reading in the design notes.
+and 2 (not 3) for n = 2: the recovery as printed, with the paper's f = 3/4 at n = 2, gives order 2
+there (f = 1 would give 3).
 """
 import math
 
