@@ -99,30 +99,38 @@ def with_tile(tables: dict, name: str, degree: int, tile) -> dict:
     return t
 
 
-def build_variants(variants: dict, workdir: str) -> dict:
-    """{tag: tables} -> {tag: path of the variant library}, compile failures left out"""
+def build_variants(variants: dict, workdir: str, jobs: int | None = None) -> dict:
+    """{tag: tables} -> {tag: path of the variant library}, compile failures left out; at most `jobs`
+    compilations at a time (default: the host's cores)"""
     lib = B.build()  # the in-tree objects of the other translation units
     common = [os.path.join(B.BUILD, f[:-3] + ".o") for f in sorted(os.listdir(B.CSRC))
               if f.endswith(".cu") and f != os.path.basename(TU)]
     assert os.path.exists(lib) and all(os.path.exists(o) for o in common)
     nvcc = B._nvcc()
-    procs = {}
-    for tag, tables in variants.items():
-        h = os.path.join(workdir, f"tiles_{tag}.h")
-        with open(h, "w") as f:
-            f.write(header(tables))
-        obj = os.path.join(workdir, f"v_{tag}.o")
-        cmd = [nvcc] + B.ARCH + B.FLAGS + ["--use_fast_math", "--pre-include", h, "-c", TU, "-o", obj]
-        log = open(obj + ".log", "w")
-        procs[tag] = (subprocess.Popen(cmd, stdout=log, stderr=subprocess.STDOUT), obj, log)
-    libs = {}
-    for tag, (p, obj, log) in procs.items():
+    jobs = max(1, jobs or os.cpu_count() or 1)
+    pending = list(variants.items())
+    running, done = {}, {}
+    while pending or running:
+        while pending and len(running) < jobs:
+            tag, tables = pending.pop(0)
+            h = os.path.join(workdir, f"tiles_{tag}.h")
+            with open(h, "w") as f:
+                f.write(header(tables))
+            obj = os.path.join(workdir, f"v_{tag}.o")
+            cmd = [nvcc] + B.ARCH + B.FLAGS + ["--use_fast_math", "--pre-include", h, "-c", TU, "-o", obj]
+            log = open(obj + ".log", "w")
+            running[tag] = (subprocess.Popen(cmd, stdout=log, stderr=subprocess.STDOUT), obj, log)
+        tag = next(iter(running))  # wait for the oldest compilation
+        p, obj, log = running.pop(tag)
         rc = p.wait()
         log.close()
-        if rc != 0:
+        done[tag] = obj if rc == 0 else None
+    libs = {}
+    for tag in variants:
+        if done.get(tag) is None:
             continue
         so = os.path.join(workdir, f"lib_{tag}.so")
-        subprocess.run([nvcc] + B.ARCH + ["-shared", "-o", so] + common + [obj, "-lcudart"], check=True)
+        subprocess.run([nvcc] + B.ARCH + ["-shared", "-o", so] + common + [done[tag], "-lcudart"], check=True)
         libs[tag] = so
     return libs
 
