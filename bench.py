@@ -371,7 +371,7 @@ def ensemble_measurement(dgx, inputs, torch, stream, steps: int, warmup: int):
 
 def side_workloads(dgx, inputs, oracle_l1, torch, stream, flush):
     """throughput of the other paths at their own sizes (FP32-bulk, L2 flushed before each timed
-    step): the shear layer with a passive dye (Sec. 3.4), the 128^3 driven turbulence box (Sec. 6,
+    step): the shear layer with a passive dye (Sec. 3.4), the 128^3 driven turbulence box (Sec. 7.1,
     3-D, working set above L2), and the metric's same-L1-error check on the 32^2 density wave."""
     import numpy as np
     out = {}

@@ -47,7 +47,9 @@ enum {
     DG_ENOMEM = 2,       /* device allocation failed                         */
     DG_ECUDA = 3,        /* a CUDA runtime call failed                       */
     DG_ENONPHYS = 4,     /* rho <= 0 or p <= 0 at a quadrature point (Sec. 4.2) */
-    DG_ETIMEOUT = 5,     /* a bounded device wait gave up                    */
+    DG_ETIMEOUT = 5,     /* reserved: no kernel of this build waits on the
+                            device (no spins, no cross-CTA flags), so no
+                            call returns it                                  */
     DG_EUNSUPPORTED = 6  /* valid request this build does not implement      */
 };
 
@@ -81,7 +83,7 @@ typedef struct dg_grid {
  *             stage (rho_bottom = 1e-6 mean rho, p_bottom = 1e-6 p(mean state),
  *             at most 60 pressure halvings; a cell that still fails, or whose
  *             mean state is non-physical, sets the status word).
- *  forcing_on: 1 adds the turbulence driving of Sec. 6: an acceleration s(x)
+ *  forcing_on: 1 adds the turbulence driving of Sec. 7.1: an acceleration s(x)
  *             of Fourier modes 2pi/L <= |k| <= 2 (2pi/L) (one of each +-k
  *             pair: 6 in 2-D, 16 in 3-D), amplitude force_amp |k|^(-5/3) with
  *             |k| in units of 2pi/L, complex vector coefficients that follow
@@ -183,7 +185,10 @@ int dg_step_timed(dg_t *h, double dt, float *ms, int nms);
 /* Wait for the handle's stream and report the device status word. */
 int dg_sync(dg_t *h);
 
-/* CFL step of Eq. timestep for the current state (FP64), no time advance. */
+/* CFL step of Eq. timestep for the current state (FP64), no time advance.
+ * The CFL factor is the handle's dg_params.cfl (set with dg_set_params), so
+ * the call takes no cfl argument; dg_max_dt_noalloc, which has no handle,
+ * takes it explicitly. */
 int dg_max_dt(dg_t *h, double *dt);
 
 /* FP64 totals sum_K |K| w[f][K][0] for the conserved fields (d+2 values). */
@@ -207,11 +212,13 @@ int dg_set_aux(dg_t *h, const double *S_prev, const double *wig, const double *s
 int dg_get_forcing(dg_t *h, double *host_state);
 int dg_set_forcing(dg_t *h, const double *host_state);
 
-/* The CFL time step of Eq. timestep, like dg_max_dt, for callers that cannot
- * let a library allocate device memory: code that hands all device memory to
- * its own pool at start-up and forbids later allocations, or time-stepping
- * loops that cannot take the device synchronisation of cudaMalloc/cudaFree.
- * The paper has no counterpart; this is a service of this library.
+/* The CFL time step dt = cfl * h_min / (2 (n+1) (max c_s + max |v|)), the
+ * maxima taken over the volume Gauss points of the state -- the same value as
+ * dg_max_dt -- for callers that cannot let a library allocate device memory:
+ * code that hands all device memory to its own pool at start-up and forbids
+ * later allocations, or time-stepping loops that cannot take the device
+ * synchronisation of cudaMalloc/cudaFree.  The paper has no counterpart; this
+ * is a service of this library.
  *
  * Needs no handle and allocates nothing.  dev_state: device pointer to the
  * FP64 state in the layout above (its first d+2 fields are read; an alpha
@@ -226,9 +233,13 @@ int dg_set_forcing(dg_t *h, const double *host_state);
  * 4.19 M cells in 3-D at degree 3, 16.7 M cells in 2-D at degree 3) return
  * DG_EUNSUPPORTED.  All calls share that array: calls whose work overlaps on
  * the GPU (different streams, or different host threads) race and must be
- * serialised by the caller.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  Returns DG_OK, DG_EINVAL, DG_EUNSUPPORTED or DG_ECUDA. */
+ * serialised by the caller.  The first call on each device does set-up work
+ * on the host: it looks up the array's device address (cudaGetSymbolAddress),
+ * and with lazy module loading it is also the call that loads the library's
+ * kernels onto that device (the array becomes resident there then) and sets
+ * the time-step kernel's shared-memory attribute.  Make that first call on a
+ * device before any stream capture on it.  Returns DG_OK, DG_EINVAL,
+ * DG_EUNSUPPORTED or DG_ECUDA. */
 int dg_max_dt_noalloc(const dg_grid *grid, int degree, double gamma, double cfl, const double *dev_state,
                       double *dev_dt, void *stream);
 

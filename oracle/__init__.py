@@ -316,7 +316,7 @@ def rhs(prob: Problem, w: np.ndarray, wig: np.ndarray | None = None, fst: np.nda
     return out, st
 
 
-# ---------------------------------------------------------------- turbulence driving (Sec. 6)
+# ---------------------------------------------------------------- turbulence driving (Sec. 7.1)
 
 def forcing_modes(dim: int) -> np.ndarray:
     """[nmodes, 3] integer wave vectors of the driving (one of every +-k pair)."""
@@ -406,7 +406,7 @@ class Sim:
     S_prev: np.ndarray = None
     wig: np.ndarray = None
     scal: np.ndarray = field(default_factory=lambda: np.zeros(3))  # dt_prev, step, t
-    fst: np.ndarray = None  # forcing state (Sec. 6 driving)
+    fst: np.ndarray = None  # forcing state (Sec. 7.1 driving)
 
     def __post_init__(self):
         self.w = np.ascontiguousarray(self.w, dtype=np.float64).copy()

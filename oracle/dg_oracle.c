@@ -81,7 +81,7 @@ typedef struct {
     int positivity_on;
     double cfl;
     int rk_stages; /* 0: automatic choice from the order */
-    /* turbulence driving (Sec. 6, "Driving"): amplitude of the |k| = 1 modes, OU correlation
+    /* turbulence driving (Sec. 7.1, "Driving"): amplitude of the |k| = 1 modes, OU correlation
      * time t_s, update interval, generator seed */
     int forcing_on;
     double force_amp, force_ts, force_dt;
@@ -579,13 +579,13 @@ static int check_cfg(const or_cfg *c)
 }
 
 /* ------------------------------------------------------------------ */
-/* Turbulence driving (Sec. 6, "Driving")                              */
+/* Turbulence driving (Sec. 7.1, "Driving")                              */
 /* ------------------------------------------------------------------ */
 /* The acceleration field is a sum of Fourier modes with wave numbers 2pi/L <= |k| <= 2 (2pi/L),
  * amplitude proportional to |k|^(-5/3), whose complex vector coefficients follow independent
  * Ornstein-Uhlenbeck processes (correlation time t_s, advanced exactly at update instants
  * j * force_dt) and are projected onto the plane normal to k (solenoidal driving, the
- * projection equation of Sec. 6).  A real field needs one mode of every +-k pair:
+ * projection equation of Sec. 7.1).  A real field needs one mode of every +-k pair:
  *   s(x) = sum_m  Re(s_m) cos(K_m.(x-lo)) - Im(s_m) sin(K_m.(x-lo)),
  *   s_m = A |k_m|^(-5/3) P(K_m) (X_m + i Y_m),  P(K) = I - K K^T / |K|^2,
  * K_m,a = 2 pi k_m,a / L_a, |k_m| in units of 2 pi / L.  X_m, Y_m are unit-variance OU
@@ -843,7 +843,7 @@ static int face_flux(const or_cfg *c, const or_tab *T, const or_geo *g, const do
 /* number of face positions along ax for a given transverse cell row */
 static int face_positions(const or_cfg *c, const or_geo *g, int ax) { return c->bc[ax] == 0 ? g->N[ax] : g->N[ax] + 1; }
 
-/* right-hand side; with fst (forcing on) the driving source of Sec. 6 is added: rho s to the
+/* right-hand side; with fst (forcing on) the driving source of Sec. 7.1 is added: rho s to the
  * momentum and rho s.v = s.(rho v) to the energy, Gauss-integrated like every volume term */
 int or_rhs_forced(const or_cfg *c, const double *w, const double *wig, const double *fst, double *rhs)
 {

@@ -5,6 +5,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <map>
@@ -224,7 +225,7 @@ struct dg_handle {
     cudaGraphExec_t graph = nullptr;
     double graph_dt = 0.0;
 
-    // turbulence driving (Sec. 6)
+    // turbulence driving (Sec. 7.1)
     ForcingModes fm;
     double *fstate = nullptr;  // [kForceState] OU state
     double *smodes = nullptr;  // [kForceModes][6] projected, scaled amplitudes
@@ -368,6 +369,18 @@ cudaError_t launch_forcing_eval_any(const dg_t *h)
 
 int prepare_kernels(dg_t *h);
 
+// Host-side fault injection for the failure paths of the allocations: with the environment
+// variable DGX_FAULT=alloc:K, the K-th device allocation of every alloc_buffers call (K >= 1)
+// fails as if cudaMalloc had reported cudaErrorMemoryAllocation, without calling it.  No device
+// fault is involved; the caller sees DG_ENOMEM and a handle that owns no device memory.
+int injected_alloc_failure()
+{
+    const char *f = getenv("DGX_FAULT");
+    if (!f || strncmp(f, "alloc:", 6) != 0) return 0;
+    const int k = atoi(f + 6);
+    return k > 0 ? k : 0;
+}
+
 int alloc_buffers(dg_t *h)
 {
     free_buffers(h);
@@ -375,7 +388,11 @@ int alloc_buffers(dg_t *h)
     h->nf = h->nc + (h->p.av_on ? 1 : 0);
     h->nw = (size_t)h->nf * h->ncell * h->M;
     const size_t rs = real_size(h);
+    const int fail_at = injected_alloc_failure();
+    int nalloc = 0;
     auto al = [&](void **p, size_t bytes) -> int {
+        if (++nalloc == fail_at)
+            return fail(h, DG_ENOMEM, "cudaMalloc(%zu bytes): injected failure (DGX_FAULT=alloc:%d)", bytes, fail_at);
         cudaError_t e = cudaMalloc(p, bytes);
         if (e != cudaSuccess) {
             cudaGetLastError();

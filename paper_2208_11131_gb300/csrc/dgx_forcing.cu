@@ -1,4 +1,4 @@
-// Turbulence driving of Sec. 6 ("Driving"): a solenoidal acceleration field made of Fourier
+// Turbulence driving of Sec. 7.1 ("Driving"): a solenoidal acceleration field made of Fourier
 // modes 2pi/L <= |k| <= 2 (2pi/L) with amplitude A |k|^(-5/3), whose complex vector
 // coefficients follow Ornstein-Uhlenbeck processes updated at times j * force_dt.
 //

@@ -5,7 +5,47 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 namespace dgx {
+
+// Launch set-up of one kernel, done once per device: cudaFuncSetAttribute applies to the current
+// device only, so a process that uses several GPUs needs the dynamic shared-memory attribute set
+// on each of them before the first launch there.  Also records the device's SM count and the
+// resident CTAs per SM of the kernel at (threads, smem).  The first launch on a device does the
+// set-up; handles and batches make that launch at creation (a launch over zero tiles), so it never
+// falls inside a stream capture.  Thread-safe.
+constexpr int kMaxDevices = 64;
+struct KernelSetup {
+    std::mutex m;
+    bool done[kMaxDevices] = {};
+    int sms[kMaxDevices] = {};
+    int blocks_per_sm[kMaxDevices] = {};
+};
+
+template <typename K>
+cudaError_t kernel_setup(KernelSetup &ks, K kernel, int threads, size_t smem, int *sms = nullptr,
+                         int *blocks_per_sm = nullptr)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(ks.m);
+    if (!ks.done[dev]) {
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&ks.sms[dev], cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ks.blocks_per_sm[dev], kernel, threads, smem);
+        if (e != cudaSuccess) return e;
+        if (ks.blocks_per_sm[dev] < 1) ks.blocks_per_sm[dev] = 1;
+        ks.done[dev] = true;
+    }
+    if (sms) *sms = ks.sms[dev];
+    if (blocks_per_sm) *blocks_per_sm = ks.blocks_per_sm[dev];
+    return cudaSuccess;
+}
 
 constexpr int kMaxDegree = 5;
 // bits of the device status word
@@ -211,7 +251,7 @@ cudaError_t launch_stage_batch_3d_f64(int degree, int av, int ns, const StageArg
                                       int nsims, int total, const Tables<double> &t, cudaStream_t s);
 cudaError_t launch_stage_batch_3d_f32(int degree, int av, int ns, const StageArgs *descs, const int *tile_off,
                                       int nsims, int total, const Tables<float> &t, cudaStream_t s);
-// ---- turbulence driving (Sec. 6), dgx_forcing.cu
+// ---- turbulence driving (Sec. 7.1), dgx_forcing.cu
 constexpr int kForceModes = 16;                  // mode stride of the forcing state (3-D count)
 constexpr int kForceState = 1 + 6 * kForceModes;  // last update index + (X_m, Y_m) per mode
 constexpr long long kForceMaxUpdates = 100000;    // per step; more sets DG_STATUS_FORCING

@@ -426,12 +426,9 @@ cudaError_t run_prologue(const PrologueArgs &a, const Tables<Real> &t, cudaStrea
     using PL = ProloguePlan<DIM, N, Real, TX, TY, TZ>;
     auto k = prologue_kernel<DIM, N, Real, TX, TY, TZ>;
     static_assert(PL::BYTES <= 227 * 1024, "prologue tile exceeds shared memory");
-    static bool attr_set = false;  // first call comes from the handle set-up, never from a graph capture
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::BYTES);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static KernelSetup ks;
+    cudaError_t e = kernel_setup(ks, k, 256, PL::BYTES);
+    if (e != cudaSuccess) return e;
     const int blocks = a.ntile[0] * a.ntile[1] * a.ntile[2];
     if (blocks == 0) return cudaSuccess;
     k<<<blocks, 256, PL::BYTES, s>>>(a, t);

@@ -181,12 +181,9 @@ cudaError_t run_limiter(const LimiterArgs &a, const Tables<Real> &t, cudaStream_
 {
     using PL = LimiterPlan<DIM, N, Real, TR>;
     auto k = limiter_kernel<DIM, N, Real, TR>;
-    static bool attr_set = false;  // first call comes from the handle set-up
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::BYTES);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static KernelSetup ks;
+    cudaError_t e = kernel_setup(ks, k, 32 * PL::CPB, PL::BYTES);
+    if (e != cudaSuccess) return e;
     if (a.ncell == 0) return cudaSuccess;
     const long long blocks = (a.ncell + PL::CPB - 1) / PL::CPB;
     k<<<(unsigned)blocks, 32 * PL::CPB, PL::BYTES, s>>>(a, t);

@@ -1,7 +1,7 @@
-// Persistent, line-oriented version of the fused right-hand-side / Runge-Kutta stage kernel.
+// Persistent, line-oriented fused right-hand-side / Runge-Kutta stage kernel.
 //
-// Same arithmetic as stage_kernel (collocated rewriting of the modal sums of
-// Eq. time_stepping_final, see dgx_kernels.cuh); different organisation for sm_103a:
+// The arithmetic is the collocated rewriting of the modal sums of Eq. time_stepping_final
+// described in dgx_kernels.cuh; its organisation for sm_103a:
 //  * one CTA loops over tiles. Plans with prefetch buffers stream the state of tile k+1 (u^n and
 //    delta, tile + halo) into shared memory with cp.async while the CTA works on tile k; plans
 //    without them (2-D FP32, two resident CTAs per SM) load a tile synchronously, straight into
@@ -576,7 +576,7 @@ __device__ __forceinline__ void stage2_body(const StageArgs *A0, const StageArgs
                     for (int f = 0; f < NC; ++f) sF[((a * NC + f) * TC + c) * NPS + j] = w * F[f];
                 }
                 if (A.force) {
-                    // driving source of Sec. 6 at this node, Gauss-weighted like the alpha source:
+                    // driving source of Sec. 7.1 at this node, Gauss-weighted like the alpha source:
                     // rho s into the momentum, s.(rho v) into the energy; the conserved part of sR
                     // is free until the residual phase, which adds it
                     const Real *fs = static_cast<const Real *>(A.force);
@@ -1023,20 +1023,10 @@ cudaError_t run_stage2(const StageArgs &a, const Tables<Real> &t, cudaStream_t s
     using PL = Stage2Plan<DIM, N, Real, AV, NSM, TX, TY, TZ, PF>;
     auto k = stage2_kernel<DIM, N, Real, AV, NSM, TX, TY, TZ, PF>;
     static_assert(PL::BYTES <= 227 * 1024, "stage2 tile exceeds shared memory");
-    static int blocks_per_sm = 0;
-    static int sms = 0;
-    if (!blocks_per_sm) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::BYTES);
-        if (e != cudaSuccess) return e;
-        int dev = 0;
-        e = cudaGetDevice(&dev);
-        if (e != cudaSuccess) return e;
-        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k, PL::NTH, PL::BYTES);
-        if (e != cudaSuccess) return e;
-        if (blocks_per_sm < 1) blocks_per_sm = 1;
-    }
+    static KernelSetup ks;
+    int sms = 0, blocks_per_sm = 0;
+    cudaError_t e = kernel_setup(ks, k, PL::NTH, PL::BYTES, &sms, &blocks_per_sm);
+    if (e != cudaSuccess) return e;
     const int tiles = a.ntile[0] * a.ntile[1] * a.ntile[2];
     if (tiles == 0) return cudaSuccess;
     const int grid = tiles < sms * blocks_per_sm ? tiles : sms * blocks_per_sm;
@@ -1053,20 +1043,10 @@ cudaError_t run_stage2_batch(const StageArgs *descs, const int *tile_off, int ns
     constexpr bool PF = stage2_prefetch<DIM, N, Real, AV, NSM, TX, TY, TZ>();
     using PL = Stage2Plan<DIM, N, Real, AV, NSM, TX, TY, TZ, PF>;
     auto k = stage2_batch_kernel<DIM, N, Real, AV, NSM, TX, TY, TZ, PF>;
-    static int blocks_per_sm = 0;
-    static int sms = 0;
-    if (!blocks_per_sm) {  // first call comes from the batch set-up, never from a graph capture
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::BYTES);
-        if (e != cudaSuccess) return e;
-        int dev = 0;
-        e = cudaGetDevice(&dev);
-        if (e != cudaSuccess) return e;
-        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k, PL::NTH, PL::BYTES);
-        if (e != cudaSuccess) return e;
-        if (blocks_per_sm < 1) blocks_per_sm = 1;
-    }
+    static KernelSetup ks;  // first call comes from the batch set-up, never from a graph capture
+    int sms = 0, blocks_per_sm = 0;
+    cudaError_t e = kernel_setup(ks, k, PL::NTH, PL::BYTES, &sms, &blocks_per_sm);
+    if (e != cudaSuccess) return e;
     if (total_tiles == 0) return cudaSuccess;
     const int grid = total_tiles < sms * blocks_per_sm ? total_tiles : sms * blocks_per_sm;
     k<<<grid, PL::NTH, PL::BYTES, s>>>(descs, tile_off, nsims, t);

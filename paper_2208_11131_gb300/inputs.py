@@ -41,7 +41,7 @@ class Workload:
     positivity_on: int = 0
     cfl: float = 0.5
     steps: int = 1
-    # turbulence driving (Sec. 6): amplitude of the |k| = 1 modes, OU correlation time, update
+    # turbulence driving (Sec. 7.1): amplitude of the |k| = 1 modes, OU correlation time, update
     # interval, generator seed
     forcing_on: int = 0
     force_amp: float = 0.0
@@ -127,7 +127,7 @@ def c3_sod_blast(N: int = 64, n: int = 3) -> Workload:
 
 
 def c4_turbulence_box(N: int = 128, n: int = 3) -> Workload:
-    """3-D periodic subsonic turbulence box, gamma=1.001, nu=kappa=1e-4, AV on, driven (Sec. 6):
+    """3-D periodic subsonic turbulence box, gamma=1.001, nu=kappa=1e-4, AV on, driven (Sec. 7.1):
     modes 1 <= |k| <= 2, amplitude 0.03 |k|^(-5/3) (rms acceleration about 0.1, which brings the
     gas started at rest with c_s = 1 to Mach ~0.3 within a few time units), OU correlation time 1,
     update interval 0.01."""
@@ -275,7 +275,7 @@ def sod_blast_ic(wl: Workload, seed: int = BASE_SEED):
 
 def rest_state(wl: Workload) -> np.ndarray:
     """modes of gas at rest with uniform density 1 and pressure 1/gamma (sound speed 1): the
-    starting state of the driven-turbulence runs of Sec. 6"""
+    starting state of the driven-turbulence runs of Sec. 7"""
     w = np.zeros(wl.shape())
     w[0, :, 0] = 1.0
     w[wl.dim + 1, :, 0] = 1.0 / (wl.gamma * (wl.gamma - 1.0))

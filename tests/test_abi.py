@@ -57,3 +57,17 @@ def test_invalid_arguments_rejected_before_any_device_call(L):
     assert L.dg_step(None, 0.0) == dgx.DG_EINVAL
     assert L.dg_default_params(None) == dgx.DG_EINVAL
     assert L.dg_status_string(dgx.DG_ENONPHYS) == b"non-physical state"
+
+
+def test_noalloc_rejects_grids_beyond_its_static_scratch_before_any_device_call(L):
+    """dg_max_dt_noalloc keeps one slot per time-step tile in a fixed 2^18-slot device array; a grid
+    that needs more tiles is refused on the host before any CUDA call (the pointers are never
+    touched).  3-D FP64 degree-5 time-step tiles are 2 x 2 x 1 cells, so 130 x 128 x 64 cells need
+    65 * 64 * 64 = 266,240 tiles."""
+    g = dgx.make_grid(3, (130, 128, 64), (0, 0, 0), (1, 1, 1))
+    fake = ctypes.c_void_p(0x1000)
+    code = L.dg_max_dt_noalloc(ctypes.byref(g), 5, 1.4, 0.3, fake, fake, None)
+    assert code == dgx.DG_EUNSUPPORTED
+    # one tile fewer than the limit along z passes the size check (it then needs a device, so only
+    # the size rule is checked here: 65 * 64 * 63 tiles are within 2^18)
+    assert 65 * 64 * 63 <= 1 << 18 < 65 * 64 * 64

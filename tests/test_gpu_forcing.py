@@ -1,4 +1,4 @@
-"""Turbulence driving (Sec. 6) on the GPU against the oracle, through the C ABI.
+"""Turbulence driving (Sec. 7.1) on the GPU against the oracle, through the C ABI.
 
 * right-hand side with a given driving state (dg_set_forcing): same tolerances as the undriven
   right-hand side (flux-term scale, FP64 1e-13, FP32-bulk 1e-5), and the driving contribution

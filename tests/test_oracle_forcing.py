@@ -1,4 +1,4 @@
-"""Pins of the oracle's turbulence driving (Sec. 6, "Driving"), CPU only.
+"""Pins of the oracle's turbulence driving (Sec. 7.1, "Driving"), CPU only.
 
 What the paper fixes: modes with 2pi/L <= |k| <= 2 (2pi/L), amplitude proportional to |k|^(-5/3),
 Ornstein-Uhlenbeck phases updated at intervals with correlation time t_s, the solenoidal

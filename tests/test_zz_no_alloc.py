@@ -62,3 +62,25 @@ def test_noalloc_reports_nonphysical_state_then_recovers():
     # the shared status word is cleared by the next call
     good = _dt_noalloc(torch, wl, w, 0.3)
     assert abs(good / _dt_handle(wl, w) - 1.0) < DT_TOL
+
+
+def test_noalloc_call_allocates_no_device_memory():
+    """The entry point's reason to exist: after the first call on a device (which may load the
+    library's kernels there), further calls leave the device's free memory unchanged."""
+    torch = pytest.importorskip("torch")
+    B.build()
+    wl = inputs.c2_shear_layer(N=64, n=3)
+    w = inputs.project(wl, inputs.shear_layer_ic(wl))
+    grid = dgx.make_grid(wl.dim, wl.N[:wl.dim], wl.lo[:wl.dim], wl.hi[:wl.dim], wl.bc[:wl.dim])
+    state = torch.from_numpy(np.ascontiguousarray(w)).cuda()
+    out = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    dgx.dg_max_dt_noalloc(grid, wl.n, wl.gamma, wl.cfl, state.data_ptr(), out.data_ptr(), stream)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        dgx.dg_max_dt_noalloc(grid, wl.n, wl.gamma, wl.cfl, state.data_ptr(), out.data_ptr(), stream)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert abs(float(out.item()) / _dt_handle(wl, w) - 1.0) < DT_TOL
