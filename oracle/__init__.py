@@ -57,6 +57,7 @@ class Cfg(ctypes.Structure):
         ("forcing_on", ctypes.c_int), ("force_amp", ctypes.c_double), ("force_ts", ctypes.c_double),
         ("force_dt", ctypes.c_double), ("force_seed", ctypes.c_ulonglong),
         ("tracer_on", ctypes.c_int), ("eta", ctypes.c_double), ("basis", ctypes.c_int),
+        ("s_floor", ctypes.c_double),
     ]
 
 FMODES = 16  # forcing-state mode stride
@@ -211,6 +212,10 @@ class Problem:
     tracer_on: int = 0
     eta: float = 0.0
     basis: int = 0  # 0 tensor product, 1 total degree l_x + l_y + l_z <= n (Sec. 2.3)
+    # floor of the oscillation sensor in the wiggle source, as a fraction of the onset threshold
+    # s_onset/P^2 (the reading of Sec. 4.1's d log S/dt; a parameter only so that tests can show
+    # what the floor does)
+    s_floor: float = 1e-4
 
     def cfg(self) -> Cfg:
         c = Cfg()
@@ -230,6 +235,7 @@ class Problem:
         c.force_seed = int(self.force_seed) & 0xFFFFFFFFFFFFFFFF
         c.tracer_on, c.eta = int(self.tracer_on), float(self.eta)
         c.basis = int(self.basis)
+        c.s_floor = float(self.s_floor)
         return c
 
     @property

@@ -92,6 +92,9 @@ typedef struct {
     /* basis (Sec. 2.3): 0 full tensor product (every l_a <= n), 1 the paper's total-degree set
      * (l_x + l_y + l_z <= n) */
     int basis;
+    /* floor of the oscillation sensor inside the logarithm of the wiggle source, as a fraction
+     * of the onset threshold s_onset/P^2 (1e-4: the reading of Sec. 4.1 used throughout) */
+    double s_floor;
 } or_cfg;
 
 /* ------------------------------------------------------------------ */
@@ -1070,7 +1073,7 @@ int or_wiggle(const or_cfg *c, const double *w, double *S_prev, double *wig, dou
     if (!S) return OR_EINVAL;
     or_sensor(c, w, S);
     double s_on = c->s_onset / ((double)g.P * g.P);
-    double s_floor = 1e-4 * s_on;
+    double s_floor = c->s_floor * s_on;
     for (long K = 0; K < g.ncell; ++K) {
         double dlog = 0.0;
         if (step > 0 && dt_prev > 0.0) dlog = (log(fmax(S[K], s_floor)) - log(fmax(S_prev[K], s_floor))) / dt_prev;
