@@ -1,21 +1,25 @@
 #!/usr/bin/env python
 """Throughput of the DG hot path: DOF-updates/s of whole SSP-RK steps on one GB300.
 
-Workload (default): the 2-D compressible Navier-Stokes shear layer with artificial viscosity,
-256 x 256 cells on [0,1] x [0,2], degree 3 (16 modes/cell), 4 conserved fields + alpha,
-SSP(5,4), CFL 0.5, FP32-bulk arithmetic with FP64 state accumulation.  A "step" is one whole
-Runge-Kutta step: five fused right-hand-side/stage kernels, the first also doing the step
-prologue (sensor, wiggle source, CFL speeds of u^n), the second starting with the dt reduction.
-DOF-updates per step = cells x modes x 4 conserved fields x 5 stages.
+Workload (default): the 3-D driven subsonic turbulence box of Sec. 7, 128^3 periodic cells, degree 3
+(64 modes/cell), 5 conserved fields + alpha, gamma = 1.001, nu = kappa = 1e-4, artificial viscosity
+on, Ornstein-Uhlenbeck driving on, SSP(5,4), CFL 0.5, FP32-bulk arithmetic with FP64 state
+accumulation.  The timed state starts turbulent: a seeded solenoidal velocity field of the wave
+vectors 1 <= |k| <= 3 scaled to rms Mach 0.3 (uniform density 1, pressure 1/gamma).  A "step" is one
+whole Runge-Kutta step: the driving update and field, five fused right-hand-side/stage kernels (the
+first also doing the step prologue: sensor, wiggle source, CFL speeds of u^n; the second starting
+with the dt reduction).  DOF-updates per step = cells x modes x 5 conserved fields x 5 stages.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dgx|reference] [--precision fp32|fp64]
+                  [--workload NAME]
 
 Timing: W untimed steps, then K steps, each timed on the device with CUDA events recorded by the
 library around its own launches (dg_step_timed), with an L2 flush (a 256 MiB device write) before
-each timed step, outside the events.  Barrier + synchronize on both sides, max over ranks.
-N > 1 runs independent replicas (the path is sharded by whole simulations; no collective on the
-data path), `value` is the sum of the units all ranks processed over the slowest rank's time.
---impl reference times the FP64 CPU oracle on the host cores (rank 0 only).
+each timed step, outside the events (the step's working set exceeds L2 in any case).  Barrier +
+synchronize on both sides, max over ranks.  N > 1 runs independent replicas (the path is sharded by
+whole simulations; no collective on the data path), `value` is the sum of the units all ranks
+processed over the slowest rank's time.  --impl reference times the FP64 CPU oracle on the host
+cores (rank 0 only) on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -51,37 +55,47 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-extras", action="store_true", help="skip the fp64 side run, e2e and cpu baseline")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched 64-member ensemble measurement")
-    ap.add_argument("--workload", default="shear_layer_256", choices=sorted(WORKLOADS),
-                    help="workload of the main measurement (the extras always use the default one)")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS),
+                    help="workload of the main measurement (the extras run with the default one only)")
     return ap.parse_args()
 
 
-# name -> (label, workload factory, initial modes); the default is the benchmark workload
+# name -> (label, workload factory, initial modes, description of the initial state)
 WORKLOADS = {
+    "turbulence_box_128": ("driven_turbulence_3d_128cubed_deg3_av_ns_forcing_mach0.3",
+                           lambda inputs: inputs.c4_turbulence_box(N=128, n=3),
+                           lambda inputs, wl: inputs.turbulence_ic_state(wl),
+                           "solenoidal random velocity, 1 <= |k| <= 3, rms Mach 0.3, rho = 1, p = 1/gamma"),
+    "turbulence_box_64": ("driven_turbulence_3d_64cubed_deg3_av_ns_forcing_mach0.3",
+                          lambda inputs: inputs.c4_turbulence_box(N=64, n=3),
+                          lambda inputs, wl: inputs.turbulence_ic_state(wl),
+                          "solenoidal random velocity, 1 <= |k| <= 3, rms Mach 0.3, rho = 1, p = 1/gamma"),
     "shear_layer_256": ("ns_shear_layer_2d_256x256_deg3_av",
                         lambda inputs: inputs.c2_shear_layer(N=256, n=3),
-                        lambda inputs, wl: inputs.project(wl, inputs.shear_layer_ic(wl))),
-    "turbulence_box_64": ("driven_turbulence_3d_64cubed_deg3_av_ns_forcing",
-                          lambda inputs: inputs.c4_turbulence_box(N=64, n=3),
-                          lambda inputs, wl: inputs.rest_state(wl)),
-    "turbulence_box_128": ("driven_turbulence_3d_128cubed_deg3_av_ns_forcing",
-                           lambda inputs: inputs.c4_turbulence_box(N=128, n=3),
-                           lambda inputs, wl: inputs.rest_state(wl)),
+                        lambda inputs, wl: inputs.project(wl, inputs.shear_layer_ic(wl)),
+                        "smooth Kelvin-Helmholtz shear layer of Sec. 6"),
+    "sod_blast_64": ("sod_plane_blast_3d_64cubed_deg3_av_limiter",
+                     lambda inputs: inputs.c3_sod_blast(N=64, n=3),
+                     lambda inputs, wl: inputs.project(wl, inputs.sod_blast_ic(wl)),
+                     "Sod plane (1, 1 | 0.125, 0.1) across a seeded plane + blast p = 100 in r < 0.1"),
 }
-DEFAULT_WORKLOAD = "shear_layer_256"
+DEFAULT_WORKLOAD = "turbulence_box_128"
 
 
 def workload(name: str = DEFAULT_WORKLOAD):
     from paper_2208_11131_gb300 import inputs
-    label, make, ic = WORKLOADS[name]
+    label, make, ic, _ = WORKLOADS[name]
     wl = make(inputs)
     return wl, (lambda: ic(inputs, wl)), label
 
 
 def config_of(wl, extra=None, label=WORKLOADS[DEFAULT_WORKLOAD][0]):
+    desc = {v[0]: v[3] for v in WORKLOADS.values()}.get(label)
     cfg = {"workload": label, "cells": list(wl.N[:wl.dim]), "degree": wl.n,
            "fields": wl.nfields, "conserved_dofs": wl.dofs, "rk_stages": 5, "nu": wl.nu, "kappa": wl.kappa,
-           "gamma": wl.gamma, "cfl": wl.cfl, "l2": "flushed before every timed step (256 MiB device write)"}
+           "gamma": wl.gamma, "cfl": wl.cfl, "av": bool(wl.av_on), "driving": bool(wl.forcing_on),
+           "positivity_limiter": bool(wl.positivity_on), "initial_state": desc,
+           "l2": "flushed before every timed step (256 MiB device write)"}
     if extra:
         cfg.update(extra)
     return cfg
@@ -243,13 +257,31 @@ def oracle_problem(wl):
     import oracle
     return oracle.Problem(dim=wl.dim, n=wl.n, N=tuple(wl.N[:wl.dim]), lo=tuple(wl.lo[:wl.dim]),
                           hi=tuple(wl.hi[:wl.dim]), bc=tuple(wl.bc[:wl.dim]), gamma=wl.gamma, nu=wl.nu,
-                          kappa=wl.kappa, av_on=wl.av_on, positivity_on=wl.positivity_on, cfl=wl.cfl)
+                          kappa=wl.kappa, av_on=wl.av_on, positivity_on=wl.positivity_on, cfl=wl.cfl,
+                          forcing_on=wl.forcing_on, force_amp=wl.force_amp, force_ts=wl.force_ts,
+                          force_dt=wl.force_dt, force_seed=wl.force_seed)
+
+
+# the oracle's bounded sample of each workload: the same physics on a grid it steps in about a second
+SAMPLE_CELLS = {"turbulence_box_128": 16, "turbulence_box_64": 16, "shear_layer_256": 256, "sod_blast_64": 16}
+
+
+def sample_workload(name: str, cells: int | None = None):
+    """the workload `name` on the oracle's sample grid (same degree, physics and initial-state recipe)"""
+    from paper_2208_11131_gb300 import inputs
+    label, make, ic, _ = WORKLOADS[name]
+    full = make(inputs)
+    N = SAMPLE_CELLS[name] if cells is None else cells
+    wl = full.with_(N=tuple([N] * full.dim + [1] * (3 - full.dim)))
+    return wl, ic(inputs, wl)
 
 
 def run_oracle_steps(wl, w0, nsteps: int, seconds: float | None = None):
     """time whole oracle steps; returns (seconds, steps done, threads)"""
     import oracle
     P = oracle_problem(wl)
+    if wl.positivity_on:
+        oracle.positivity(P, w0)
     sim = oracle.Sim(P, w0)
     t0 = time.perf_counter()
     done = 0
@@ -263,25 +295,66 @@ def run_oracle_steps(wl, w0, nsteps: int, seconds: float | None = None):
     return time.perf_counter() - t0, done, oracle.num_threads()
 
 
+def cpu_baseline(name: str):
+    """the oracle as it stands on the host cores: all cores on the workload's sample grid for about
+    12 s, and one core on an 8-cell-per-axis (3-D) or 64^2 (2-D) grid for about 8 s"""
+    import oracle
+    wl, w0 = sample_workload(name)
+    secs, done, cores = run_oracle_steps(wl, w0, 1000, seconds=12.0)
+    out = {"value": wl.dofs * 5 * done / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{'x'.join(str(c) for c in wl.N[:wl.dim])} cells of the same workload (same degree, "
+                     f"physics and initial-state recipe), {done} whole FP64 SSP(5,4) steps; per-DOF cost "
+                     f"of the oracle does not depend on the grid size"}
+    wl1, w1 = sample_workload(name, 8 if wl.dim == 3 else 64)
+    prev = oracle.num_threads()
+    oracle.set_threads(1)
+    try:
+        secs1, done1, _ = run_oracle_steps(wl1, w1, 1000, seconds=8.0)
+    finally:
+        oracle.set_threads(prev)
+    out["one_core"] = {"value": wl1.dofs * 5 * done1 / secs1, "unit": UNIT, "cores": 1,
+                       "sample": f"{'x'.join(str(c) for c in wl1.N[:wl1.dim])} cells, {done1} steps"}
+    return out
+
+
 def reference_arm(args, rank, ws):
     if rank != 0:
         return
-    import numpy as np  # noqa: F401
-    from paper_2208_11131_gb300 import inputs
-    wl, ic, _ = workload()
-    w0 = ic()
-    run_oracle_steps(wl, w0, args.warmup)
-    secs, done, cores = run_oracle_steps(wl, w0, args.steps)
+    name = getattr(args, "workload", DEFAULT_WORKLOAD)
+    wl_full, _, label = workload(name)
+    wl, w0 = sample_workload(name)
+    run_oracle_steps(wl, w0.copy(), args.warmup)
+    secs, done, cores = run_oracle_steps(wl, w0.copy(), args.steps)
     units = wl.dofs * 5 * done
     value = units / secs
-    sample = f"full 256x256 grid, {done} whole SSP(5,4) steps per timed run"
+    sample = (f"{'x'.join(str(c) for c in wl.N[:wl.dim])} cells of the same workload, {done} whole FP64 SSP(5,4) "
+              f"steps per timed run (the full grid takes minutes per oracle step)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": done, "warmup": args.warmup, "ms_per_step": 1e3 * secs / done, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_of(wl, {"engine": "FP64 CPU oracle (C, OpenMP)"}),
+            "config": config_of(wl_full, {"engine": "FP64 CPU oracle (C, OpenMP)"}, label=label),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def alu_peaks():
+    """FP32 and FP64 FMA-chain throughput (TFLOP/s) of this GPU, from the probe library built next to
+    libdgx.so; None where it is missing"""
+    import ctypes
+    path = os.path.join(ROOT, "paper_2208_11131_gb300", "libdgxpeak.so")
+    try:
+        L = ctypes.CDLL(path)
+    except OSError:
+        return None
+    L.dgx_fma_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    out = {}
+    for name, fp64, iters in (("fp32_tflops", 0, 1 << 16), ("fp64_tflops", 1, 1 << 12)):
+        v = ctypes.c_double()
+        if L.dgx_fma_peak(fp64, iters, 5, ctypes.byref(v)) == 0:
+            out[name] = v.value
+    out["how"] = "FMA chains (8 per thread) over every SM, best of 5 launches, CUDA events"
+    return out
 
 
 def step_working_set_bytes(nvals: int, fp32: bool) -> int:
@@ -369,37 +442,58 @@ def ensemble_measurement(dgx, inputs, torch, stream, steps: int, warmup: int):
             "l2": "not flushed; the members' state alone exceeds L2"}
 
 
-def side_workloads(dgx, inputs, oracle_l1, torch, stream, flush):
+def n_launches(wl, stages: int = 5) -> int:
+    """kernel launches the library makes per step for a workload: the driving update and field (when
+    driving is on), the stage kernels (the first with the step prologue folded in, unless the limiter
+    is on: then a prologue, a dt reduction and a limiter after every stage and on the state entering
+    the step)"""
+    n = stages + (2 if wl.forcing_on else 0)
+    if wl.positivity_on:
+        n += 2 + stages + 1
+    return n
+
+
+def timed_steps(dgx, wl, w0, steps, warm, stream, flush, prec=None):
+    """(per-step launch times [steps][7] in ms, state after) of whole steps through dg_step_timed"""
+    sim = dgx.Simulation(wl, precision=dgx.DG_FP32_BULK if prec is None else prec)
+    sim.set_stream(stream)
+    sim.set_state(w0)
+    for _ in range(warm):
+        dgx.dg_step_timed(sim.h, 0.0, 7)
+    per = []
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        per.append(dgx.dg_step_timed(sim.h, 0.0, 7))
+    sim.sync()
+    return per, sim
+
+
+def path_line(wl, per, label, fp32=True, peak=None):
+    """ms per step, value and the stage-launch HBM roofline of a measured path"""
+    import numpy as np
+    ms = float(np.mean([sum(x) for x in per]))
+    stage_ms = float(np.mean([sum(x[2:]) for x in per]))
+    out = {"workload": label, "ms_per_step": ms, "value": wl.dofs * 5 / (ms / 1e3), "unit": UNIT,
+           "steps": len(per), "launch_ms_mean": [float(np.mean([x[i] for x in per])) for i in range(7)]}
+    if peak:
+        nvals = wl.nfields * wl.ncell * wl.M
+        out["roofline"] = stage_roofline(nvals, wl.ncell, fp32, stage_ms, peak)
+        out["working_set_bytes"] = step_working_set_bytes(nvals, fp32)
+    return out
+
+
+def side_workloads(dgx, inputs, oracle_l1, torch, stream, flush, peak):
     """throughput of the other paths at their own sizes (FP32-bulk, L2 flushed before each timed
-    step): the shear layer with a passive dye (Sec. 3.4), the 128^3 driven turbulence box (Sec. 7.1,
-    3-D, working set above L2), and the metric's same-L1-error check on the 32^2 density wave."""
+    step): the 2-D NS shear layer (Sec. 6) and the same with a passive dye (Sec. 3.4), the 64^3 Sod
+    plane + blast with the positivity limiter (Sec. 4.2; the limiter launches are inside the stage
+    slots), and the metric's same-L1-error check on the 32^2 density wave."""
     import numpy as np
     out = {}
-
-    def timed(wl, w0, steps, warm, stages):
-        sim = dgx.Simulation(wl, precision=dgx.DG_FP32_BULK)
-        sim.set_stream(stream)
-        sim.set_state(w0)
-        for _ in range(warm):
-            dgx.dg_step_timed(sim.h, 0.0, 7)
-        ms, stage_ms = [], []
-        for k in range(steps):
-            flush.fill_(k & 0xFF)
-            t = dgx.dg_step_timed(sim.h, 0.0, 7)
-            ms.append(sum(t))
-            stage_ms.append(sum(t[2:]))  # the stage launches (slots 0, 1: driving, prologue)
+    for name, steps, warm in (("shear_layer_256", 20, 5), ("sod_blast_64", 6, 2)):
+        wl, ic, label = workload(name)
+        per, sim = timed_steps(dgx, wl, ic(), steps, warm, stream, flush)
         sim.close()
-        m = float(np.mean(ms))
-        out = {"ms_per_step": m, "value": wl.dofs * stages / (m / 1e3), "unit": UNIT, "steps": steps}
-        if stages == 5:
-            try:
-                peak = float(measured_peaks()[0]["hbm_gbs"])
-                out["roofline"] = stage_roofline(wl.nfields * wl.ncell * wl.M, wl.ncell, True,
-                                                 float(np.mean(stage_ms)), peak)
-                out["working_set_bytes"] = step_working_set_bytes(wl.nfields * wl.ncell * wl.M, True)
-            except Exception as e:  # a side figure never costs the benchmark line
-                out["roofline_error"] = repr(e)
-        return out
+        out[name] = path_line(wl, per, label, True, peak)
 
     wl = inputs.c2_shear_layer(N=256, n=3).with_(tracer_on=1, eta=1e-5)
     w = inputs.project(wl.with_(tracer_on=0), inputs.shear_layer_ic(wl.with_(tracer_on=0)))
@@ -409,11 +503,9 @@ def side_workloads(dgx, inputs, oracle_l1, torch, stream, flush):
     rc = np.zeros_like(c)
     rc[:, 0] = w[0, :, 0] * c[:, 0]  # rho c from the cell means (a dye of the layers)
     w0 = np.ascontiguousarray(np.concatenate([w[:4], rc[None], w[4:]]))
-    out["tracer"] = dict(timed(wl, w0, 10, 3, 5), workload="ns_shear_layer_2d_256x256_deg3_av_with_dye")
-
-    wl = inputs.c4_turbulence_box(N=128, n=3)
-    out["turbulence_box"] = dict(timed(wl, inputs.rest_state(wl), 4, 2, 5),
-                                 workload="driven_turbulence_3d_128cubed_deg3_av_ns_forcing")
+    per, sim = timed_steps(dgx, wl, w0, 10, 3, stream, flush)
+    sim.close()
+    out["tracer"] = path_line(wl, per, "ns_shear_layer_2d_256x256_deg3_av_with_dye", True, peak)
 
     wl = inputs.c1_density_wave(N=32, n=2)
     w0 = inputs.project(wl, inputs.density_wave_ic(wl, 0.0))
@@ -469,6 +561,8 @@ def dgx_arm(args, rank, ws, local):
     barrier(ws)
     clk = clocks.stop()
     sim.sync()
+    aux = sim.get_aux()
+    state = sim.get_state()
     step_ms = [sum(x) for x in per_launch]
     total_ms, value = job_value(sum(step_ms), wl.dofs * 5 * args.steps, ws)
     stage_ms = sum(sum(x[2:]) for x in per_launch)
@@ -486,6 +580,7 @@ def dgx_arm(args, rank, ws, local):
             "algorithmic_bytes_per_launch": stage_bytes / 5,
             "avg_launch_ms": stage_ms / launches,
             "share_of_step": stage_ms / sum(step_ms)}
+    vel = state[1:1 + wl.dim, :, 0] / state[0, :, 0]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64", "data": "synthetic",
@@ -496,17 +591,20 @@ def dgx_arm(args, rank, ws, local):
                                        "l2_bytes": l2_bytes(local),
                                        "l2_resident": l2_resident(step_working_set_bytes(nvals, fp32), local)}),
             "roofline": roof, "clocks": clk,
-            # launches the library made per step: folded-away slots of dg_step_timed read 0
-            "gpu_launches": args.steps * sum(1 for i in range(nl) if np.mean([x[i] for x in per_launch]) > 0),
+            "gpu_launches": args.steps * n_launches(wl),
             "launch_ms_mean": [float(np.mean([x[i] for x in per_launch])) for i in range(nl)],
-            "wall_ms_per_step": 1e3 * t_wall / args.steps}
+            # host time of the timed loop: each step is one dg_step_timed call, which waits for the
+            # step's last event, plus the L2 flush fill launched before it
+            "wall_ms_per_step": 1e3 * t_wall / args.steps,
+            "state_after_timed_steps": {"t": float(aux[2][2]), "steps_taken": int(aux[2][1]),
+                                        "rms_cell_mean_speed": float(np.sqrt((vel ** 2).sum(0).mean()))}}
 
     if not args.no_extras and default:
         # end to end through the public C ABI with pinned host buffers: H2D state, one step, D2H state
         host_in = torch.from_numpy(w0).pin_memory()
         host_out = torch.empty_like(host_in).pin_memory()
         a_in, a_out = host_in.numpy(), host_out.numpy()
-        e2e_steps = max(3, min(args.steps, 10))
+        e2e_steps = 3
         dgx.dg_set_state(sim.h, a_in)
         dgx.dg_step(sim.h, 0.0)
         dgx.dg_get_state(sim.h, a_out)
@@ -520,6 +618,7 @@ def dgx_arm(args, rank, ws, local):
         nbytes = a_in.nbytes
         line["e2e"] = {"value": wl.dofs * 5 * e2e_steps * ws / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                        "d2h_bytes_per_step": nbytes, "steps": e2e_steps}
+        del host_in, host_out, a_in, a_out
         # the other precision on the same workload, and the FP32-bulk vs FP64 difference
         other = dgx.Simulation(wl, precision=dgx.DG_FP64 if fp32 else dgx.DG_FP32_BULK)
         other.set_stream(stream)
@@ -528,7 +627,7 @@ def dgx_arm(args, rank, ws, local):
         ref.set_stream(stream)
         ref.set_state(w0)
         ms_other = []
-        nsteps_cmp = 10
+        nsteps_cmp = 6
         for k in range(nsteps_cmp):
             t = dgx.dg_step_timed(other.h, 0.0, nl)
             if k >= 2:
@@ -541,19 +640,17 @@ def dgx_arm(args, rank, ws, local):
         line["other_precision"] = {"dtype": "f64" if fp32 else "f32", "ms_per_step": other_ms,
                                    "value": wl.dofs * 5 / (other_ms / 1e3), "unit": UNIT,
                                    "steps": nsteps_cmp - 2}
-        line["fp32_vs_fp64_rel_l1_rho_after_10_steps"] = l1
+        line[f"fp32_vs_fp64_rel_l1_rho_after_{nsteps_cmp}_steps"] = l1
         other.close()
         ref.close()
+        line["alu_peaks"] = alu_peaks()
         if rank == 0 and ws == 1:
-            secs, done, cores = run_oracle_steps(wl, w0, 40, seconds=15.0)
-            line["cpu_baseline"] = {"value": wl.dofs * 5 * done / secs, "unit": UNIT, "cores": cores,
-                                    "kind": "oracle",
-                                    "sample": f"full 256x256 grid, {done} whole FP64 SSP(5,4) steps"}
+            line["cpu_baseline"] = cpu_baseline(args.workload)
     sim.close()
     if not args.no_ensemble and default:
         line["ensemble"] = ensemble_measurement(dgx, inputs, torch, stream, steps=20, warmup=3)
     if not args.no_extras and default and rank == 0:
-        line["other_paths"] = side_workloads(dgx, inputs, l1_error_of, torch, stream, flush)
+        line["other_paths"] = side_workloads(dgx, inputs, l1_error_of, torch, stream, flush, peak)
     if rank == 0:
         print(json.dumps(line), flush=True)
 

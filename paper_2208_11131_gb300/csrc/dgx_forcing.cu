@@ -126,28 +126,33 @@ __global__ void forcing_update_kernel(const ForcingModes fm, int dim, double dec
     }
 }
 
-template <int DIM, typename Real>
-__global__ void __launch_bounds__(256) forcing_eval_kernel(int Q, int N0, int N1, long long ncell, const Real *tab,
+// one thread per volume node; Q is a compile-time constant, so the node split of the flat index
+// is a multiplication, and the cell split uses 32-bit arithmetic (cells < 2^31)
+template <int DIM, int Q, typename Real>
+__global__ void __launch_bounds__(256) forcing_eval_kernel(int N0, int N1, long long ncell, const Real *tab,
                                                            long long off1, long long off2, const double *smodes,
                                                            Real *out)
 {
     constexpr ModeList<DIM> ML = mode_list<DIM>();
+    constexpr int NP = DIM == 2 ? Q * Q : Q * Q * Q;
     __shared__ Real sm[6 * kForceModes];
     for (int i = threadIdx.x; i < 6 * kForceModes; i += blockDim.x) sm[i] = (Real)smodes[i];
     __syncthreads();
-    const int NP = DIM == 2 ? Q * Q : Q * Q * Q;
     const long long total = ncell * NP;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
-        const long long cell = idx / NP;
-        const int j = (int)(idx - cell * NP);
-        const int c0 = (int)(cell % N0), c1 = (int)((cell / N0) % N1), c2 = (int)(cell / ((long long)N0 * N1));
+        const int cell = (int)(idx / NP);
+        const int j = (int)(idx - (long long)cell * NP);
+        const int c01 = cell / N0;
+        const int c0 = cell - c01 * N0;
+        const int c2 = c01 / N1;
+        const int c1 = c01 - c2 * N1;
         const int j0 = j % Q, j1 = (j / Q) % Q, j2 = j / (Q * Q);
         // exp(i K_a x_a) for k_a = -2..2 at this node, per axis
         Real er[3][5], ei[3][5];
-        const Real *t0 = tab + ((long long)c0 * Q + j0) * 10;
-        const Real *t1 = tab + off1 + ((long long)c1 * Q + j1) * 10;
-        const Real *t2 = tab + off2 + ((long long)c2 * Q + j2) * 10;
+        const Real *t0 = tab + (c0 * Q + j0) * 10;
+        const Real *t1 = tab + off1 + (c1 * Q + j1) * 10;
+        const Real *t2 = tab + off2 + (c2 * Q + j2) * 10;
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
             er[0][k] = t0[2 * k];
@@ -176,21 +181,41 @@ __global__ void __launch_bounds__(256) forcing_eval_kernel(int Q, int N0, int N1
     }
 }
 
+template <int DIM, int Q, typename Real>
+cudaError_t launch_eval(const int *N, long long ncell, const Real *tab, const long long *off, const double *smodes,
+                        Real *out, cudaStream_t s)
+{
+    constexpr int NP = DIM == 2 ? Q * Q : Q * Q * Q;
+    const long long total = ncell * NP;
+    long long blocks = (total + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) return cudaSuccess;
+    forcing_eval_kernel<DIM, Q, Real><<<(unsigned)blocks, 256, 0, s>>>(N[0], N[1], ncell, tab, off[1],
+                                                                        DIM == 3 ? off[2] : 0, smodes, out);
+    return cudaGetLastError();
+}
+
+template <int DIM, typename Real>
+cudaError_t launch_eval_dim(int degree, const int *N, long long ncell, const Real *tab, const long long *off,
+                            const double *smodes, Real *out, cudaStream_t s)
+{
+    switch (degree) {
+    case 0: return launch_eval<DIM, 1, Real>(N, ncell, tab, off, smodes, out, s);
+    case 1: return launch_eval<DIM, 2, Real>(N, ncell, tab, off, smodes, out, s);
+    case 2: return launch_eval<DIM, 3, Real>(N, ncell, tab, off, smodes, out, s);
+    case 3: return launch_eval<DIM, 4, Real>(N, ncell, tab, off, smodes, out, s);
+    case 4: return launch_eval<DIM, 5, Real>(N, ncell, tab, off, smodes, out, s);
+    case 5: return launch_eval<DIM, 6, Real>(N, ncell, tab, off, smodes, out, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 template <typename Real>
 cudaError_t run_forcing_eval(int dim, int degree, const int *N, long long ncell, const Real *tab, const long long *off,
                              const double *smodes, Real *out, cudaStream_t s)
 {
-    const int Q = degree + 1;
-    const long long total = ncell * (dim == 2 ? Q * Q : Q * Q * Q);
-    long long blocks = (total + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    if (blocks < 1) return cudaSuccess;
-    if (dim == 2)
-        forcing_eval_kernel<2, Real><<<(unsigned)blocks, 256, 0, s>>>(Q, N[0], N[1], ncell, tab, off[1], 0, smodes, out);
-    else
-        forcing_eval_kernel<3, Real>
-            <<<(unsigned)blocks, 256, 0, s>>>(Q, N[0], N[1], ncell, tab, off[1], off[2], smodes, out);
-    return cudaGetLastError();
+    if (dim == 2) return launch_eval_dim<2, Real>(degree, N, ncell, tab, off, smodes, out, s);
+    return launch_eval_dim<3, Real>(degree, N, ncell, tab, off, smodes, out, s);
 }
 
 }  // namespace

@@ -282,6 +282,76 @@ def rest_state(wl: Workload) -> np.ndarray:
     return w
 
 
+def turbulence_modes(seed: int = BASE_SEED + 6, kmax2: int = 9, slope: float = -11.0 / 6.0):
+    """Seeded solenoidal Fourier amplitudes of a random velocity field on the unit periodic cube:
+    integer wave vectors with 1 <= |k|^2 <= kmax2 (|k| <= 3), one of each +-k pair (first non-zero
+    component positive), complex vector amplitudes with normal real and imaginary parts times
+    |k|^slope (slope -11/6: a k^(-5/3) shell spectrum), projected onto the plane normal to k.
+    Returns (k [nm, 3] int, A [nm, 3] complex); v(x) = sum_m Re(A_m exp(2 pi i k_m . x))."""
+    ks = []
+    for kz in range(-3, 4):
+        for ky in range(-3, 4):
+            for kx in range(-3, 4):
+                k2 = kx * kx + ky * ky + kz * kz
+                first = kx if kx != 0 else (ky if ky != 0 else kz)
+                if 1 <= k2 <= kmax2 and first > 0:
+                    ks.append((kx, ky, kz))
+    k = np.array(ks, dtype=np.int64)
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((len(k), 3)) + 1j * rng.standard_normal((len(k), 3))
+    kk = k.astype(np.float64)
+    A *= (np.sqrt((kk * kk).sum(1)) ** slope)[:, None]
+    A -= kk * ((A * kk).sum(1) / (kk * kk).sum(1))[:, None]
+    return k, A
+
+
+def turbulence_ic_state(wl: Workload, v_rms: float = 0.3, seed: int = BASE_SEED + 6) -> np.ndarray:
+    """Modes of the driven-turbulence box started already turbulent: uniform density 1 and pressure
+    1/gamma (sound speed 1) with the solenoidal random velocity of ``turbulence_modes`` scaled to the
+    rms speed v_rms (rms Mach number v_rms), on a periodic cube.  Projected with the n+3 point Gauss
+    rule like ``project``, but by separable per-axis tables of exp(2 pi i k x), one z-layer of cells
+    at a time (128^3 cells at degree 3 take some tens of seconds)."""
+    assert wl.dim == 3 and wl.basis == 0
+    k, A = turbulence_modes(seed)
+    A = A * (v_rms / np.sqrt(0.5 * np.sum(np.abs(A) ** 2)))  # <|v|^2> = sum |A|^2 / 2
+    n, q = wl.n, wl.n + 3
+    Q = n + 1
+    x, g = npleg.leggauss(q)
+    Bp = 0.5 * (g[:, None] * _pt_table(n, x))  # [q, Q]: (1/2) int over one axis of a cell
+    N = wl.N
+    L = [wl.hi[a] - wl.lo[a] for a in range(3)]
+    # per-axis phase tables E[a][kk + 3][cell * q + j] = exp(2 pi i kk x_j / L_a)
+    E = []
+    for a in range(3):
+        X = wl.lo[a] + (np.arange(N[a])[:, None] + 0.5 + 0.5 * x[None, :]) * (L[a] / N[a])
+        E.append(np.exp(2j * np.pi * np.arange(-3, 4)[:, None] * X.reshape(1, -1) / L[a]))
+    # amplitudes on the dense 7^3 cube of wave vectors
+    C = np.zeros((7, 7, 7, 3), dtype=np.complex128)
+    for m in range(len(k)):
+        C[k[m, 0] + 3, k[m, 1] + 3, k[m, 2] + 3] += A[m]
+    T1 = np.einsum("xX,xyzc->Xyzc", E[0], C)          # [Nx q, ky, kz, c]
+    T2 = np.einsum("Xyzc,yY->cXYz", T1, E[1])         # [c, Nx q, Ny q, kz]
+    T2r = np.ascontiguousarray(T2.real).reshape(-1, 7)
+    T2i = np.ascontiguousarray(T2.imag).reshape(-1, 7)
+    del T1, T2
+    nf = wl.nfields
+    out = np.zeros((nf, N[2], N[1], N[0], Q, Q, Q))   # [f][cz][cy][cx][lz][ly][lx]
+    p0 = 1.0 / wl.gamma
+    for cz in range(N[2]):
+        Ez = E[2][:, cz * q:(cz + 1) * q]              # [kz, q]
+        v = T2r @ Ez.real - T2i @ Ez.imag              # Re of the kz sum
+        v = v.reshape(3, N[0], q, N[1], q, q)           # [c][cx][jx][cy][jy][jz]
+        fields = [None, v[0], v[1], v[2], p0 / (wl.gamma - 1.0) + 0.5 * (v * v).sum(0)]
+        for f in range(1, 5):
+            # (1/|K|) int_K u phi_l: (1/2) g_j Pt_l(x_j) summed along each axis in turn (z, y, x)
+            t = np.tensordot(fields[f], Bp, axes=([4], [0]))   # [cx, jx, cy, jy, lz]
+            t = np.tensordot(t, Bp, axes=([3], [0]))           # [cx, jx, cy, lz, ly]
+            t = np.tensordot(t, Bp, axes=([1], [0]))           # [cx, cy, lz, ly, lx]
+            out[f, cz] = t.transpose(1, 0, 2, 3, 4)
+    out[0, :, :, :, 0, 0, 0] = 1.0
+    return np.ascontiguousarray(out.reshape(nf, wl.ncell, Q * Q * Q))
+
+
 def sod_tube_ic(wl: Workload, axis: int = 0, x0: float = 0.5):
     """planar Sod shock tube along one axis (the 1-D Riemann problem embedded in 2-D/3-D)"""
     def f(X):

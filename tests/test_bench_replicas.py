@@ -38,6 +38,7 @@ def _rank(rank, ws, port, out_dir):
     total_ms, value = bench.job_value(local_ms, 1000, w)
     wl = inputs.c2_shear_layer(N=8, n=3)
     bench.workload = lambda name=None: (wl, lambda: inputs.project(wl, inputs.shear_layer_ic(wl)), "tiny")
+    bench.sample_workload = lambda name, cells=None: (wl, inputs.project(wl, inputs.shear_layer_ic(wl)))
     buf = io.StringIO()
     with contextlib.redirect_stdout(buf):
         bench.reference_arm(argparse.Namespace(warmup=1, steps=2, gpus=w), r, w)

@@ -153,9 +153,10 @@ def test_ensemble_full_manifest_batched_and_oracle():
     dgx.dg_batch_sync(batch)
     for sa, sb, m in zip(a, b, members):
         assert state_err(sb.get_state(), sa.get_state(), problem(m.wl)) < 2e-5
-    # the smallest smooth and the smallest shock-tube member against the oracle (FP32-bulk vs FP64;
-    # the shock tolerance as for the FP32-bulk shock tests)
-    for kind, tol in (("wave", 1e-5), ("sod", 1e-4)):
+    # the smallest smooth and the smallest shock-tube member against the oracle (FP32-bulk vs FP64,
+    # the stated 1e-5 relative L1 in density; measured 1.7e-7 on the shock tube after 50 steps with no
+    # artificial-viscosity switch decision flipped)
+    for kind, tol in (("wave", 1e-5), ("sod", 1e-5)):
         k = min((i for i in range(len(members)) if members[i].kind == kind), key=lambda i: members[i].wl.dofs)
         ref = oracle.Sim(problem(members[k].wl), w0s[k])
         for _ in range(3):

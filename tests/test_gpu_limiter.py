@@ -84,6 +84,8 @@ def test_sod_blast_3d_fp32_bulk_tracks_fp64():
         a.step()
         b.step()
     wa, wb = a.get_state(), b.get_state()
-    assert rel_l1(wb, wa, 0) < 1e-4
+    # the stated FP32-bulk tolerance, 1e-5 relative L1 in density (measured 5.8e-8 after 30 steps,
+    # no sensor or wiggle-source switch flipped between the precisions)
+    assert rel_l1(wb, wa, 0) < 1e-5
     a.close()
     b.close()

@@ -74,7 +74,7 @@ def test_total_degree_shock_tube_steps_with_limiter(prec):
     if prec == dgx.DG_FP64:
         assert state_err(out, ref.w, P) < 1e-11
     else:
-        assert rel_l1(out, ref.w, 0) < 1e-4
+        assert rel_l1(out, ref.w, 0) < 1e-5  # the stated FP32-bulk tolerance (measured 1.9e-7 at 20 steps)
     sim.close()
 
 
