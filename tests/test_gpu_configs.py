@@ -100,13 +100,17 @@ def test_turbulence_box_100_steps_and_spectrum(N):
     Er, E64, E32 = (velocity_spectrum(wl, w) for w in (ref.w, o64, o32))
     tot = Er.sum()
     assert Er[1:4].sum() > 0.5 * tot  # the energy sits in the driven and initial shells
-    d64 = np.abs(E64 - Er) / (Er + 1e-12 * tot)
-    d32 = np.abs(E32 - Er) / (Er + 1e-9 * tot)
-    print(f"spectrum {N}^3: max rel shell difference fp64 {d64.max():.3e} fp32-bulk {d32.max():.3e}")
-    # state errors of 1e-11 (FP64) and 1e-5 (FP32-bulk) move a shell's power by at most twice that
-    # relative to it, plus the absolute floors for the nearly empty shells
-    assert d64.max() < 1e-9
-    assert d32.max() < 1e-4
+    # a relative state error e moves the power of a shell by at most about 2 e times the total (the
+    # cross term of the difference field with the velocity, Cauchy-Schwarz); in the energetic shells
+    # (over 1% of the total) also relative to the shell itself.  e: the stated 1e-11 (FP64) and 1e-5
+    # (FP32-bulk); nearly empty shells can differ more relative to themselves
+    big = Er > 0.01 * tot
+    for name, E, e in (("fp64", E64, FP64_TOL), ("fp32-bulk", E32, FP32_TOL)):
+        d_tot = np.abs(E - Er).max() / tot
+        d_big = (np.abs(E - Er)[big] / Er[big]).max()
+        print(f"spectrum {N}^3 {name}: max shell difference / total {d_tot:.3e}, "
+              f"/ shell (energetic shells) {d_big:.3e}")
+        assert d_tot < 2 * e and d_big < 2 * e, (name, d_tot, d_big)
 
 
 def test_ensemble_50_steps():
