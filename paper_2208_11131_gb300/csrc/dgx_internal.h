@@ -97,7 +97,9 @@ enum StageConst {
 struct StageArgs {
     int N[3];      // cells per axis (1 for unused axes)
     int bc[3];     // 0 periodic, 1 outflow
-    int ntile[3];  // tiles per axis
+    int ntile[3];  // tiles per axis (the z-marching kernel: columns along x, y and chunks along z)
+    int zchunk;    // z-marching kernel: planes per chunk
+    int reserved_;
     double h[3];
     double hmin;
     double gamma, nu, kappa;
