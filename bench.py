@@ -392,13 +392,13 @@ def rk_stages_for(n: int) -> int:
     return {0: 1, 1: 2, 2: 3}.get(n, 5)
 
 
-def ensemble_measurement(dgx, inputs, torch, stream, steps: int, warmup: int):
+def ensemble_measurement(dgx, inputs, torch, stream, steps: int, warmup: int, log2_cells=(6, 10), label=None):
     """64 independent 2-D runs of mixed size (64..512 cells per axis), degree (1..5) and physics
     (density wave / Sod tube, Euler+AV / NS+AV), FP32-bulk: whole SSP-RK steps of all members, batched
     (one persistent stage kernel per (degree, physics) group over every member's tiles, per-member
     device dt, CUDA graph) against the same members stepped one after another on the same stream.
     Both are timed with CUDA events on that stream around `steps` whole steps."""
-    members = inputs.c5_manifest(count=64)
+    members = inputs.c5_manifest(count=64, log2_cells=log2_cells)
     sims = []
     for m in members:
         s = dgx.Simulation(m.wl, precision=dgx.DG_FP32_BULK)
@@ -433,7 +433,7 @@ def ensemble_measurement(dgx, inputs, torch, stream, steps: int, warmup: int):
     dgx.dg_batch_destroy(batch)
     for s in sims:
         s.close()
-    return {"workload": "ensemble_64_mixed_2d_deg1to5_fp32bulk", "members": len(members),
+    return {"workload": label or "ensemble_64_mixed_2d_deg1to5_fp32bulk", "members": len(members),
             "cells_per_axis": sorted({m.wl.N[0] for m in members}),
             "dof_updates_per_step": units, "state_bytes": state_bytes, "steps": steps, "warmup": warmup,
             "batched": {"ms_per_step": ms_b, "value": units / (ms_b / 1e3), "unit": UNIT},
@@ -649,6 +649,10 @@ def dgx_arm(args, rank, ws, local):
     sim.close()
     if not args.no_ensemble and default:
         line["ensemble"] = ensemble_measurement(dgx, inputs, torch, stream, steps=20, warmup=3)
+        # where batching pays: 64 members of 32^2 to 128^2 cells, each too small to fill the GPU alone
+        line["ensemble_small"] = ensemble_measurement(dgx, inputs, torch, stream, steps=20, warmup=3,
+                                                      log2_cells=(5, 8),
+                                                      label="ensemble_64_small_2d_32to128_deg1to5_fp32bulk")
     if not args.no_extras and default and rank == 0:
         line["other_paths"] = side_workloads(dgx, inputs, l1_error_of, torch, stream, flush, peak)
     if rank == 0:

@@ -244,17 +244,20 @@ int dg_max_dt_noalloc(const dg_grid *grid, int degree, double gamma, double cfl,
                       double *dev_dt, void *stream);
 
 /* Batched ensembles: many independent simulations advanced together.
- * Members are grouped by (dim, degree, precision, AV, NS); each group runs one
- * persistent stage kernel per Runge-Kutta stage over the work list of all its
- * members' tiles, with each member's own time step (CFL of its own state, or
- * the fixed dt) computed on the device.  Groups run concurrently; dg_batch_step
- * replays two whole steps at a time from one captured CUDA graph.  Members keep
- * their own state and may be read with dg_get_state after dg_batch_sync.
- * All members must share the device, the stream and the step parity (same
- * number of steps taken so far modulo 2) and have at least two Runge-Kutta
- * stages; the positivity limiter is not available in batches
- * (DG_EUNSUPPORTED).  The batch does not own the members: destroy it before
- * them.  The arithmetic of every member is the same as with dg_step. */
+ * Members are grouped by (dim, degree, precision, AV, NS, limiter); each group
+ * runs one persistent stage kernel per Runge-Kutta stage over the work list of
+ * all its members' tiles, with each member's own time step (CFL of its own
+ * state, or the fixed dt) computed on the device.  Members with the positivity
+ * limiter (Sec. 4.2) form groups of their own: each member's step prologue and
+ * limiter launches run on the group's stream around the batched stage launches.
+ * Groups run concurrently; dg_batch_step replays two whole steps at a time from
+ * one captured CUDA graph.  Members keep their own state and may be read with
+ * dg_get_state after dg_batch_sync.  All members must share the device, the
+ * stream and the step parity (same number of steps taken so far modulo 2) and
+ * have at least two Runge-Kutta stages; driving and tracer members are not
+ * available in batches (DG_EUNSUPPORTED).  The batch does not own the members:
+ * destroy it before them.  The arithmetic of every member is the same as with
+ * dg_step. */
 typedef struct dg_batch dg_batch_t;
 int dg_batch_create(dg_t *const *sims, int count, dg_batch_t **out);
 int dg_batch_step(dg_batch_t *b, int nsteps, double dt); /* enqueues only */

@@ -604,6 +604,53 @@ void fill_stage_args(const dg_t *h, const Schedule &S, int i, int c, bool fused,
     }
 }
 
+// positivity limiter of the state entering a step (only initial data can need it: every later u^n
+// is a limited stage output)
+LimiterArgs entry_limiter_args(const dg_t *h)
+{
+    LimiterArgs la;
+    memset(&la, 0, sizeof la);
+    la.ncell = h->ncell;
+    la.gamma = h->gamma;
+    la.tracer_on = h->p.tracer_on;
+    la.last = 1;
+    la.ufull = h->U[h->cur];
+    la.uhi = fp32(h) ? h->Uhi[h->cur] : nullptr;
+    la.status = h->status;
+    return la;
+}
+
+// positivity limiter after stage i of a step that starts from state buffer c
+LimiterArgs stage_limiter_args(const dg_t *h, const Schedule &S, int i, int c)
+{
+    const StageDesc &d = S.s[i];
+    const int nx = 1 - c;
+    LimiterArgs la;
+    memset(&la, 0, sizeof la);
+    la.ncell = h->ncell;
+    la.gamma = h->gamma;
+    la.tracer_on = h->p.tracer_on;
+    la.last = d.last;
+    la.ubase = fp32(h) ? (const void *)h->Uhi[c] : (const void *)h->U[c];
+    la.delta = d.last ? nullptr : h->D[d.out];
+    la.ufull = d.last ? h->U[nx] : nullptr;
+    la.uhi = d.last && fp32(h) ? h->Uhi[nx] : nullptr;
+    la.status = h->status;
+    return la;
+}
+
+// the separate step prologue (the path with the limiter, or one stage): limiter of the entering
+// state, sensor + wiggle source + per-block CFL maxima, and the dt reduction -> dtp
+int enqueue_prologue_dt(dg_t *h, double dt)
+{
+    if (h->p.positivity_on) CK(h, launch_limiter_any(h, entry_limiter_args(h)));
+    CK(h, launch_prologue_any(h, 1));
+    dt_kernel<<<1, 256, 0, h->stream>>>(h->partial, h->pblocks, dt > 0.0 ? dt : 0.0, h->p.cfl, h->hmin,
+                                        h->degree + 1, h->dtp, 1, h->status);
+    CK(h, cudaGetLastError());
+    return DG_OK;
+}
+
 // enqueue one full step on h->stream (no host synchronisation).  With `ev`, an event is recorded
 // before the first launch (ev[0]) and after each launch in launch order (ev[1..]).
 //
@@ -626,19 +673,7 @@ int enqueue_step(dg_t *h, double dt, cudaEvent_t *ev = nullptr)
         if (ev) CK(h, cudaEventRecord(ev[ne++], h->stream));
     }
     if (!fused) {
-        if (h->p.positivity_on) {
-            // the state entering the step is limited too (only initial data can need it)
-            LimiterArgs la;
-            memset(&la, 0, sizeof la);
-            la.ncell = h->ncell;
-            la.gamma = h->gamma;
-            la.tracer_on = h->p.tracer_on;
-            la.last = 1;
-            la.ufull = h->U[h->cur];
-            la.uhi = fp32(h) ? h->Uhi[h->cur] : nullptr;
-            la.status = h->status;
-            CK(h, launch_limiter_any(h, la));
-        }
+        if (h->p.positivity_on) CK(h, launch_limiter_any(h, entry_limiter_args(h)));
         CK(h, launch_prologue_any(h, 1));
         if (ev) CK(h, cudaEventRecord(ev[ne++], h->stream));
         dt_kernel<<<1, 256, 0, h->stream>>>(h->partial, h->pblocks, dt > 0.0 ? dt : 0.0, h->p.cfl, h->hmin,
@@ -660,20 +695,7 @@ int enqueue_step(dg_t *h, double dt, cudaEvent_t *ev = nullptr)
         }
         int grid = 0;
         CK(h, launch_stage_any(h, a, &grid));
-        if (h->p.positivity_on) {
-            LimiterArgs la;
-            memset(&la, 0, sizeof la);
-            la.ncell = h->ncell;
-            la.gamma = h->gamma;
-            la.tracer_on = h->p.tracer_on;
-            la.last = d.last;
-            la.ubase = a.ubase;
-            la.delta = d.last ? nullptr : h->D[d.out];
-            la.ufull = d.last ? h->U[nx] : nullptr;
-            la.uhi = d.last && fp32(h) ? h->Uhi[nx] : nullptr;
-            la.status = h->status;
-            CK(h, launch_limiter_any(h, la));
-        }
+        if (h->p.positivity_on) CK(h, launch_limiter_any(h, stage_limiter_args(h, S, i, c)));
         if (ev) CK(h, cudaEventRecord(ev[ne++], h->stream));
         if (fused && i == 0) {
             if (grid > h->partial_cap) return fail(h, DG_EINVAL, "stage grid %d exceeds %d", grid, h->partial_cap);
@@ -1143,6 +1165,7 @@ const char *dg_last_error(const dg_t *h)
 struct dg_batch {
     struct Group {
         int dim = 2, degree = 0, prec = 0, av = 0, ns = 0, stages = 0;
+        int lim = 0;  // positivity limiter: separate step prologue per member, limiter after every stage
         std::vector<int> members;
         int total_tiles = 0;
         StageArgs *d_desc = nullptr;  // [2 parities][stages][members]
@@ -1190,8 +1213,35 @@ int enqueue_batch_step(dg_batch_t *b, double dt, cudaStream_t origin)
     if (cudaEventRecord(b->fork, origin) != cudaSuccess) return bfail(b, DG_ECUDA, "cudaEventRecord");
     for (auto &g : b->groups) {
         if (cudaStreamWaitEvent(g.st, b->fork, 0) != cudaSuccess) return bfail(b, DG_ECUDA, "cudaStreamWaitEvent");
+        // members of a limiter group issue their own prologue and limiter launches on the group's stream
+        auto on_group_stream = [&](dg_t *h, auto fn) -> int {
+            cudaStream_t own = h->stream;
+            h->stream = g.st;
+            const int r = fn(h);
+            h->stream = own;
+            return r;
+        };
+        if (g.lim) {
+            for (int m : g.members) {
+                dg_t *h = b->sims[m];
+                if (on_group_stream(h, [&](dg_t *hh) { return enqueue_prologue_dt(hh, dt); }))
+                    return bfail(b, DG_ECUDA, h->err.c_str());
+            }
+        }
+        const Schedule S = schedule_for(g.stages);
         for (int i = 0; i < g.stages; ++i) {
             if (launch_batch_group(g, b->parity, i, g.st) != cudaSuccess) return bfail(b, DG_ECUDA, "batched stage launch");
+            if (g.lim) {
+                for (int m : g.members) {
+                    dg_t *h = b->sims[m];
+                    const int r = on_group_stream(h, [&](dg_t *hh) -> int {
+                        CK(hh, launch_limiter_any(hh, stage_limiter_args(hh, S, i, b->parity)));
+                        return DG_OK;
+                    });
+                    if (r) return bfail(b, DG_ECUDA, "member limiter launch");
+                }
+                continue;
+            }
             if (i == 0) {
                 const StageArgs *d = g.d_desc + (size_t)b->parity * g.stages * g.members.size();
                 batch_dt_kernel<<<1, 256, 0, g.st>>>(d, (int)g.members.size(), g.degree + 1, dt > 0.0 ? dt : 0.0);
@@ -1231,7 +1281,7 @@ int dg_batch_create(dg_t *const *sims, int count, dg_batch_t **out)
     for (int k = 0; k < count; ++k) {
         const dg_t *h = sims[k];
         if (!h) return DG_EINVAL;
-        if (h->p.positivity_on || h->p.forcing_on || h->p.tracer_on || stage_count(h) < 2) return DG_EUNSUPPORTED;
+        if (h->p.forcing_on || h->p.tracer_on || stage_count(h) < 2) return DG_EUNSUPPORTED;
         if (h->cur != sims[0]->cur || h->device != sims[0]->device || h->stream != sims[0]->stream)
             return DG_EINVAL;
     }
@@ -1240,11 +1290,11 @@ int dg_batch_create(dg_t *const *sims, int count, dg_batch_t **out)
     b->sims.assign(sims, sims + count);
     b->stream = sims[0]->stream;
     b->parity = sims[0]->cur;
-    std::map<std::tuple<int, int, int, int, int>, int> key_to_group;
+    std::map<std::tuple<int, int, int, int, int, int>, int> key_to_group;
     for (int k = 0; k < count; ++k) {
         const dg_t *h = sims[k];
         const int ns = (h->nu > 0.0 || h->kappa > 0.0) ? 1 : 0;
-        const auto key = std::make_tuple(h->dim, h->degree, (int)fp32(h), h->p.av_on, ns);
+        const auto key = std::make_tuple(h->dim, h->degree, (int)fp32(h), h->p.av_on, ns, h->p.positivity_on);
         auto it = key_to_group.find(key);
         if (it == key_to_group.end()) {
             dg_batch::Group g;
@@ -1254,6 +1304,7 @@ int dg_batch_create(dg_t *const *sims, int count, dg_batch_t **out)
             g.av = h->p.av_on;
             g.ns = ns;
             g.stages = stage_count(h);
+            g.lim = h->p.positivity_on;
             g.rep = h;
             it = key_to_group.emplace(key, (int)b->groups.size()).first;
             b->groups.push_back(g);
@@ -1282,8 +1333,10 @@ int dg_batch_create(dg_t *const *sims, int count, dg_batch_t **out)
             for (int i = 0; i < g.stages; ++i)
                 for (int m = 0; m < nm; ++m) {
                     StageArgs &a = host[((size_t)par * g.stages + i) * nm + m];
-                    fill_stage_args(sims[g.members[m]], S, i, par, true, a);
-                    if (i == 0) a.partial = g.d_max + 2 * m;  // per-simulation maxima (atomics)
+                    // without the limiter the step prologue is folded into the first stage; with it the
+                    // members run the separate prologue and the stages read each member's dt
+                    fill_stage_args(sims[g.members[m]], S, i, par, !g.lim, a);
+                    if (i == 0 && !g.lim) a.partial = g.d_max + 2 * m;  // per-simulation maxima (atomics)
                     stage_consts(a, g.degree, g.dim);
                 }
         if (cudaMemcpy(g.d_off, off.data(), sizeof(int) * (nm + 1), cudaMemcpyHostToDevice) != cudaSuccess ||

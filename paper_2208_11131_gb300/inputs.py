@@ -414,14 +414,15 @@ class Member:
     axis: int  # shock-tube axis
 
 
-def c5_manifest(seed: int = BASE_SEED, count: int = 64):
-    """64 independent 2-D runs: cells per axis drawn from {64,128,256,512} (log-uniform), degree
-    uniform in 1..5, half smooth density waves (periodic) and half Sod tubes along a seeded axis
-    (outflow along it), half of all members with NS (nu = kappa = 1e-4); AV on for all."""
+def c5_manifest(seed: int = BASE_SEED, count: int = 64, log2_cells=(6, 10)):
+    """64 independent 2-D runs: cells per axis drawn from {64,128,256,512} (log-uniform; log2_cells
+    gives the half-open range of log2 of the cells per axis), degree uniform in 1..5, half smooth
+    density waves (periodic) and half Sod tubes along a seeded axis (outflow along it, positivity
+    limiter on), half of all members with NS (nu = kappa = 1e-4); AV on for all."""
     rng = np.random.default_rng(seed + 5)
     out = []
     for i in range(count):
-        N = int(2 ** rng.integers(6, 10))
+        N = int(2 ** rng.integers(*log2_cells))
         n = int(rng.integers(1, 6))
         kind = "wave" if rng.random() < 0.5 else "sod"
         axis = int(rng.integers(0, 2))
@@ -433,7 +434,7 @@ def c5_manifest(seed: int = BASE_SEED, count: int = 64):
             gamma = 1.4
         nu = 1e-4 if ns else 0.0
         wl = Workload(f"member{i}", 2, n, (N, N, 1), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), bc=bc, gamma=gamma, nu=nu,
-                      kappa=nu, av_on=1, cfl=0.3, steps=50)
+                      kappa=nu, av_on=1, cfl=0.3, steps=50, positivity_on=1 if kind == "sod" else 0)
         out.append(Member(wl, kind, axis))
     return out
 

@@ -31,8 +31,9 @@ def small_members():
     for i, (N, n, kind, axis, nu) in enumerate(specs):
         bc = (0, 0, 0) if kind == "wave" else ((1, 0, 0) if axis == 0 else (0, 1, 0))
         g = 5.0 / 3.0 if kind == "wave" else 1.4
+        # shock-tube members run with the positivity limiter (Sec. 4.2), as in the ensemble workload
         wl = inputs.Workload(f"m{i}", 2, n, (N, N, 1), (0, 0, 0), (1.0, 1.0, 1.0), bc=bc, gamma=g, nu=nu, kappa=nu,
-                             av_on=1, cfl=0.3)
+                             av_on=1, cfl=0.3, positivity_on=1 if kind == "sod" else 0)
         out.append(inputs.Member(wl, kind, axis))
     return out
 
@@ -99,8 +100,32 @@ def test_batch_members_match_oracle():
         s.close()
 
 
-def test_batch_rejects_limiter_members():
-    wl = inputs.Workload("lim", 2, 2, (8, 8, 1), (0, 0, 0), (1.0, 1.0, 1.0), gamma=1.4, av_on=1, positivity_on=1)
+def test_batch_with_limiter_members_matches_oracle():
+    """limiter members form groups of their own (separate step prologue per member, limiter after
+    every batched stage) next to the folded-prologue groups of the other members"""
+    members = [m for m in small_members() if m.kind == "sod"][:2] + [small_members()[0]]
+    assert any(m.wl.positivity_on for m in members) and not all(m.wl.positivity_on for m in members)
+    sims = [dgx.Simulation(m.wl) for m in members]
+    refs = []
+    for s, m in zip(sims, members):
+        w0 = inputs.member_state(m)
+        s.set_state(w0)
+        refs.append(oracle.Sim(problem(m.wl), w0))
+    batch = dgx.dg_batch_create([s.h for s in sims])
+    dgx.dg_batch_step(batch, 5)
+    dgx.dg_batch_sync(batch)
+    for s, r, m in zip(sims, refs, members):
+        for _ in range(5):
+            _, st = r.step()
+            assert st == 0
+        assert state_err(s.get_state(), r.w, problem(m.wl)) < 1e-11
+    dgx.dg_batch_destroy(batch)
+    for s in sims:
+        s.close()
+
+
+def test_batch_rejects_forced_members():
+    wl = inputs.c4_turbulence_box(N=4, n=1)
     s = dgx.Simulation(wl)
     with pytest.raises(dgx.DGError) as e:
         dgx.dg_batch_create([s.h])
