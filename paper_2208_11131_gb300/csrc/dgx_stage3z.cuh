@@ -6,10 +6,11 @@
 //
 //  * a cell's Q^2 x-lines fit in one warp.  Lane group g of a warp owns one cell, lane gl of the
 //    group one x-line (y, z) = (gl % Q, gl / Q), held in registers.  Every exchange inside a cell
-//    -- the y and z passes of the modal<->nodal transforms (through the cell's own shared-memory
-//    slot, ordered by __syncwarp), the nodal gradients along y and z and the weak divergence of
-//    the y and z fluxes (Q x Q products across the lanes of the group with xor shuffles) -- needs
-//    no block barrier;
+//    -- the y and z passes of the modal<->nodal transforms, the nodal gradients along y and z and
+//    the weak divergence of the y and z fluxes -- is a Q x Q product across the Q lanes that differ
+//    in one index, done with xor shuffles, and needs no shared memory and no barrier.  Shared
+//    memory holds each cell's nodal values once, for the face phases (lines xor-swizzled so that
+//    the strided face-line reads are free of bank conflicts);
 //  * a CTA owns a column of TX x TY cells and marches along z through a chunk of planes.  Each
 //    plane is loaded and transformed once as the "next" plane, used for the z-faces of the plane
 //    below it, and then becomes the current plane; only the x/y face-neighbour ring (2 (TX + TY)
@@ -69,6 +70,18 @@ __device__ __forceinline__ float xmatvec(float v, const float (&Mx)[Q])
     return acc;
 }
 
+// Offset of the x-line (y, z) of one field inside a cell slot.  The Q^2 lines of Q values are
+// permuted by an xor swizzle (degree 3: lines with z >= 2 swap y <-> y ^ 2) so that the strided
+// reads of the face phases -- the Q lanes of one y-line or z-line position taking the same element
+// of different lines -- fall on distinct shared-memory banks; whole-line vector accesses are
+// unaffected.
+template <int Q>
+__device__ __forceinline__ int z3_line(int y, int z)
+{
+    const int sy = Q == 4 ? (z & 2) : 0;
+    return ((y ^ sy) + Q * z) * Q;
+}
+
 // the Q values of field f of a cell slot along axis a through the node position (p0, p1) of the
 // face numbering (a = 0: x-line at (y, z) = (p0, p1); 1: y-line at (x, z); 2: z-line at (x, y))
 template <int Q, int a>
@@ -78,13 +91,13 @@ __device__ __forceinline__ void z3_axis_line(const float *slot, int f, int p0, i
     constexpr int VEC = (Q * 4) % 16 == 0 ? 16 : 8;
     const float *b = slot + f * NP;
     if constexpr (a == 0) {
-        ld_line<Q, VEC>(b + (p0 + Q * p1) * Q, v);
+        ld_line<Q, VEC>(b + z3_line<Q>(p0, p1), v);
     } else if constexpr (a == 1) {
 #pragma unroll
-        for (int m = 0; m < Q; ++m) v[m] = b[p0 + Q * (m + Q * p1)];
+        for (int m = 0; m < Q; ++m) v[m] = b[z3_line<Q>(m, p1) + p0];
     } else {
 #pragma unroll
-        for (int m = 0; m < Q; ++m) v[m] = b[p0 + Q * (p1 + Q * m)];
+        for (int m = 0; m < Q; ++m) v[m] = b[z3_line<Q>(p1, m) + p0];
     }
 }
 
@@ -391,39 +404,24 @@ __global__ void __launch_bounds__(256, 2) stage3z_kernel(const StageArgs A, cons
 #pragma unroll
             for (int i = 0; i < Q; ++i) w[f][i] = o[i];
         }
-        // y then z through the slot: store the lane's line, read the Q lines along the axis
+        // y then z across the group's lanes (xor shuffles): out(i) = sum_m B[i][m] v(m), the lane of
+        // index i holding v(i)
         float by[Q], bz[Q];
 #pragma unroll
-        for (int m = 0; m < Q; ++m) {
-            by[m] = tB[ly * Q + m];
-            bz[m] = tB[lz * Q + m];
+        for (int k = 0; k < Q; ++k) {
+            by[k] = tB[ly * Q + (ly ^ k)];
+            bz[k] = tB[lz * Q + (lz ^ k)];
         }
 #pragma unroll
-        for (int pass = 0; pass < 2; ++pass) {
+        for (int f = 0; f < NF; ++f)
 #pragma unroll
-            for (int f = 0; f < NF; ++f) st_line<Q, VEC>(slot + f * NP + gl * Q, w[f]);
-            __syncwarp();
+            for (int i = 0; i < Q; ++i) w[f][i] = xmatvec<Q, 1>(w[f][i], by);
 #pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                float o[Q];
+        for (int f = 0; f < NF; ++f) {
 #pragma unroll
-                for (int i = 0; i < Q; ++i) o[i] = 0.0f;
-#pragma unroll
-                for (int m = 0; m < Q; ++m) {
-                    float t[Q];
-                    const int line = pass == 0 ? m + Q * lz : ly + Q * m;
-                    ld_line<Q, VEC>(slot + f * NP + line * Q, t);
-                    const float c = pass == 0 ? by[m] : bz[m];
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) o[i] = fmaf(c, t[i], o[i]);
-                }
-#pragma unroll
-                for (int i = 0; i < Q; ++i) w[f][i] = o[i];
-            }
-            __syncwarp();
+            for (int i = 0; i < Q; ++i) w[f][i] = xmatvec<Q, Q>(w[f][i], bz);
+            st_line<Q, VEC>(slot + f * NP + z3_line<Q>(ly, lz), w[f]);
         }
-#pragma unroll
-        for (int f = 0; f < NF; ++f) st_line<Q, VEC>(slot + f * NP + gl * Q, w[f]);
     };
 
     // z-face between the lane group's cell in slot sl (below) and slot sr (above), at the face point
@@ -617,7 +615,7 @@ __global__ void __launch_bounds__(256, 2) stage3z_kernel(const StageArgs A, cons
                 const int g = gOwn(cur)[grp];
                 float u[NF][Q];
 #pragma unroll
-                for (int f = 0; f < NF; ++f) ld_line<Q, VEC>(slot + f * NP + gl * Q, u[f]);
+                for (int f = 0; f < NF; ++f) ld_line<Q, VEC>(slot + f * NP + z3_line<Q>(ly, lz), u[f]);
                 float dy[Q], dz[Q], wy[Q], wz[Q];
 #pragma unroll
                 for (int k = 0; k < Q; ++k) {
@@ -739,38 +737,17 @@ __global__ void __launch_bounds__(256, 2) stage3z_kernel(const StageArgs A, cons
                         }
                     }
                 }
-                // nodal -> modal: z then y through the cell's slot (dead after the loads above), x in registers
-                float cy_[Q], cz_[Q];
+                // nodal -> modal: z then y across the group's lanes, out(l) = sum_i B[i][l] r(i); x in registers
+                float cz_[Q], cy_[Q];
 #pragma unroll
-                for (int m = 0; m < Q; ++m) {
-                    cy_[m] = tB[m * Q + ly];
-                    cz_[m] = tB[m * Q + lz];
+                for (int k = 0; k < Q; ++k) {
+                    cz_[k] = tB[(lz ^ k) * Q + lz];
+                    cy_[k] = tB[(ly ^ k) * Q + ly];
                 }
-                __syncwarp();
 #pragma unroll
-                for (int pass = 0; pass < 2; ++pass) {
+                for (int f = 0; f < NF; ++f)
 #pragma unroll
-                    for (int f = 0; f < NF; ++f) st_line<Q, VEC>(slot + f * NP + gl * Q, r[f]);
-                    __syncwarp();
-#pragma unroll
-                    for (int f = 0; f < NF; ++f) {
-                        float o[Q];
-#pragma unroll
-                        for (int i = 0; i < Q; ++i) o[i] = 0.0f;
-#pragma unroll
-                        for (int m = 0; m < Q; ++m) {
-                            float t[Q];
-                            const int line = pass == 0 ? ly + Q * m : m + Q * lz;
-                            ld_line<Q, VEC>(slot + f * NP + line * Q, t);
-                            const float c = pass == 0 ? cz_[m] : cy_[m];
-#pragma unroll
-                            for (int i = 0; i < Q; ++i) o[i] = fmaf(c, t[i], o[i]);
-                        }
-#pragma unroll
-                        for (int i = 0; i < Q; ++i) r[f][i] = o[i];
-                    }
-                    __syncwarp();
-                }
+                    for (int i = 0; i < Q; ++i) r[f][i] = xmatvec<Q, 1>(xmatvec<Q, Q>(r[f][i], cz_), cy_);
                 if (mine) {
                     // epilogue on the modal x-line (l_y, l_z) = (ly, lz)
 #pragma unroll
