@@ -545,6 +545,47 @@ __global__ void __launch_bounds__(256, 2) stage3z_kernel(const StageArgs A, cons
             }
             __syncthreads();
 
+            // L2 prefetch, one plane step ahead, of the global arrays the next step reads: the halo ring of
+            // plane z + 1 and the own cells of plane z + 2 (stage input and input delta, every field),
+            // and the epilogue operands of plane z + 1 (u^n in FP64 in the last stage, the auxiliary
+            // register); each task is one contiguous run of cells of one field of one array
+            {
+                const int zh = zplane(z + 1), zo = z + 2 < z1 ? zplane(z + 2) : -1;
+                constexpr int NT = 2 * TY + 4;  // row tasks: own rows + x-halo cells + y-halo rows (max)
+                for (int t = tid; t < NT * NF * 4; t += NTH) {
+                    const int row = t % NT, f = (t / NT) % NF, arr = t / (NT * NF);
+                    int g0 = -1, nc = 0;
+                    if (row < TY) {  // own row of plane z + 2 (inputs) or z + 1 (epilogue operands)
+                        const int zz = arr < 2 ? zo : (z + 1 < z1 ? zh : -1);
+                        if (row < V1 && zz >= 0) {
+                            g0 = gcell(o0, o1, 0, row, zz);
+                            nc = V0;
+                        }
+                    } else if (arr < 2 && zh >= 0) {  // halo ring of plane z + 1
+                        const int h = row - TY;
+                        if (h < 2 * TY) {
+                            const int cy = h % TY;
+                            if (cy < V1) {
+                                g0 = gcell(o0, o1, h < TY ? -1 : V0, cy, zh);
+                                nc = 1;
+                            }
+                        } else {
+                            g0 = gcell(o0, o1, 0, h == 2 * TY ? -1 : V1, zh);
+                            nc = V0;
+                        }
+                    }
+                    if (g0 < 0) continue;
+                    const void *base = arr == 0 ? (const void *)ub : arr == 1 ? (const void *)di
+                                     : arr == 2 ? (A.mode == 2 ? (const void *)A.uold : nullptr)
+                                                : (readx ? (const void *)xb : nullptr);
+                    if (!base) continue;
+                    const size_t es = arr == 2 ? sizeof(double) : sizeof(float);
+                    const char *p = static_cast<const char *>(base) + ((size_t)f * fstride + (size_t)g0 * NP) * es;
+                    const unsigned bytes = (unsigned)(nc * NP * es);
+                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+                }
+            }
+
             // slot of tile position (cx, cy) of plane z for the face phases (halo positions included)
             auto slot_at = [&](int cx, int cy) -> const float * {
                 int s = -1;
