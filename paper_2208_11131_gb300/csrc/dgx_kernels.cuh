@@ -225,6 +225,44 @@ __device__ __forceinline__ void ns_flux(const Real *u, const Real (*grad)[DIM + 
     if constexpr (TR) F[DIM + 2] = eta * (grad[a][DIM + 2] - u[DIM + 2] * inv * grad[a][0]);
 }
 
+// Navier-Stokes fluxes along all DIM axes at one point (the rows of ns_flux for a = 0..DIM-1),
+// with the velocity gradient and its divergence formed once: F[a][f]
+template <int DIM, typename Real>
+__device__ __forceinline__ void ns_flux_all(const Real *u, const Real (*grad)[DIM + 2], Real gamma, Real nu,
+                                            Real kappa, Real (*F)[DIM + 2])
+{
+    const Real rho = u[0];
+    const Real inv = Real(1) / rho;
+    Real v[DIM], dv[DIM][DIM];
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) v[b] = u[1 + b] * inv;
+    Real div = Real(0);
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) dv[b][c] = (grad[b][1 + c] - v[c] * grad[b][0]) * inv;
+        div += dv[b][b];
+    }
+    const Real nr = nu * rho;
+    const Real eint = u[DIM + 1] * inv;
+    const Real kg = kappa * (gamma - Real(1)) * rho;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        Real work = Real(0);
+        F[a][0] = Real(0);
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+            Real pi = nr * (dv[a][c] + dv[c][a] - (c == a ? Real(2.0 / 3.0) * div : Real(0)));
+            F[a][1 + c] = pi;
+            work += v[c] * pi;
+        }
+        Real duint = (grad[a][DIM + 1] - eint * grad[a][0]) * inv;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) duint -= v[c] * dv[a][c];
+        F[a][DIM + 1] = work + kg * duint;
+    }
+}
+
 // ------------------------------------------------------------------ shared memory plan
 
 template <int DIM, int N, typename Real, int TX, int TY, int TZ>
