@@ -18,13 +18,12 @@
 //    lifted into the plane above at the next step, so every z-face is computed once.
 //
 // Per plane: (L) load + transform the halo ring of plane z and the own cells of plane z+1;
-// (F) every face of the step -- the x- and y-faces of plane z and the z-face above each own cell --
-// one face per lane group, lane gl at one face point, the recovered state's tangential derivatives
-// across the group's lanes; (V) per own cell and x-line: gradients, Euler - NS - AV flux at the
-// line's Q nodes, weak divergence, sources, lifts of the six faces, nodal->modal transform and the
-// Runge-Kutta epilogue.  Three block barriers per plane.  x/y faces on a column boundary are
-// computed by both columns with the same code from the same data, so they are bitwise equal on
-// both sides (conservation without atomics).
+// (R) recovered interface state of the x/y faces (Navier-Stokes), and the top z-face flux of
+// every own cell by the cell's lane group; (F) x/y face fluxes; (V) per own cell and x-line:
+// gradients, Euler - NS - AV flux at the line's Q nodes, weak divergence, sources, lifts of the
+// six faces, nodal->modal transform and the Runge-Kutta epilogue.  Four block barriers per plane.
+// x/y faces on a column boundary are computed by both columns with the same code from the same
+// data, so they are bitwise equal on both sides (conservation without atomics).
 #pragma once
 
 #include <stdlib.h>
@@ -45,15 +44,17 @@ struct Z3Plan {
     static constexpr int NSLOT = 2 * TC + NH;
     static constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1), NFXY = NFX + NFY;
     static constexpr int FH = NC * NFXY * G;            // x/y face fluxes [field][face][point]
+    static constexpr int UT = NS ? NC * NFXY * G : 0;   // recovered state at x/y face points
     static constexpr int FZ = 2 * NC * TC * G;          // z-face fluxes [buffer][field][cell][point]
     static constexpr int TAB = 64;                      // lane tables (B, Dn, Wd, G, Lm, Lp)
     static constexpr int OFF_FH = NSLOT * SLOT;
-    static constexpr int OFF_FZ = OFF_FH + FH;
+    static constexpr int OFF_UT = OFF_FH + FH;
+    static constexpr int OFF_FZ = OFF_UT + UT;
     static constexpr int OFF_WIG = OFF_FZ + FZ;         // [buffer][cell] wiggle source
     static constexpr int OFF_TAB = OFF_WIG + 2 * TC;
     static constexpr int NREAL = OFF_TAB + 6 * TAB;
     static constexpr size_t BYTES = sizeof(float) * (size_t)NREAL + sizeof(int) * (size_t)NSLOT;
-    static_assert((OFF_FH * 4) % 16 == 0 && (OFF_FZ * 4) % 16 == 0,
+    static_assert((OFF_FH * 4) % 16 == 0 && (OFF_UT * 4) % 16 == 0 && (OFF_FZ * 4) % 16 == 0,
                   "vector accesses need 16-byte aligned arrays");
 };
 
@@ -61,11 +62,11 @@ struct Z3Plan {
 // index bits selected by STRIDE = 1 (low) or Q (high)): returns sum_k M[i][i ^ k] v(i ^ k) with
 // Mx[k] = M[i][i ^ k] of this lane's index i
 template <int Q, int STRIDE>
-__device__ __forceinline__ float xmatvec(float v, const float (&Mx)[Q], unsigned mask = 0xffffffffu)
+__device__ __forceinline__ float xmatvec(float v, const float (&Mx)[Q])
 {
     float acc = Mx[0] * v;
 #pragma unroll
-    for (int k = 1; k < Q; ++k) acc = fmaf(Mx[k], __shfl_xor_sync(mask, v, k * STRIDE), acc);
+    for (int k = 1; k < Q; ++k) acc = fmaf(Mx[k], __shfl_xor_sync(0xffffffffu, v, k * STRIDE), acc);
     return acc;
 }
 
@@ -188,34 +189,38 @@ __device__ __forceinline__ void z3_face_flux(const float *sl, const float *sr, i
     }
 }
 
-// One face normal to axis a by one lane group, lane gl at the face point (p0, p1) = (gl % Q, gl / Q)
-// (x-face: (y, z); y-face: (x, z); z-face: (x, y)).  With NS the recovered state of Sec. 3.2 and its
-// derivatives along the two tangential axes (across the group's lanes: Dn rows dp0, dp1 of the
-// lane's indices in xor order, shuffles over the group's lanes `gmask`) enter the face flux; the
-// flux, weighted for the lift, goes to out[f * ostride + gl].  Either side may be absent.
-template <int Q, bool AV, bool NS, int a>
-__device__ __forceinline__ void z3_face_task(const float *sl, const float *sr, int p0, int p1, const float (&dp0)[Q],
-                                             const float (&dp1)[Q], unsigned gmask, const float *tG,
-                                             const Tables<float> &Tg, const StageArgs &A, float *out, int ostride,
-                                             int &bad)
+// flux of one x- (a = 0) or y- (a = 1) face point, weighted for the lift, into sFh; with NS the
+// recovered state and its tangential derivatives come from sUt (face numbering (p0, p1))
+template <int Q, bool AV, bool NS, int NFXY, int a>
+__device__ __forceinline__ void z3_xy_flux(const float *sl, const float *sr, int face, int p0, int p1, int k,
+                                           const float *sUt, const float *tDn, const float *tG,
+                                           const Tables<float> &Tg, const StageArgs &A, float *sFh, int &bad)
 {
-    constexpr int NC = 5;
-    constexpr int t0 = a == 0 ? 1 : 0, t1 = a == 2 ? 1 : 2;  // tangential axes of p0 and p1
+    constexpr int NC = 5, G = Q * Q;
+    constexpr int ta = a == 0 ? 1 : 0;  // first tangential axis (p0); the second is z (p1)
     float ut[NC], gtan[3][NC];
     if (NS && sl && sr) {
-        z3_recover<Q, a>(sl, sr, p0, p1, Tg, ut);
+        const float *pf = sUt + face * G;
 #pragma unroll
         for (int f = 0; f < NC; ++f) {
+            const float *pp = pf + f * NFXY * G;
+            ut[f] = pp[p0 + Q * p1];
+            float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+            for (int m = 0; m < Q; ++m) {
+                a0 = fmaf(tDn[p0 * Q + m], pp[m + Q * p1], a0);
+                a1 = fmaf(tDn[p1 * Q + m], pp[p0 + Q * m], a1);
+            }
             gtan[a][f] = 0.0f;
-            gtan[t0][f] = xmatvec<Q, 1>(ut[f], dp0, gmask) * A.kf[SK_TWO_H + t0];
-            gtan[t1][f] = xmatvec<Q, Q>(ut[f], dp1, gmask) * A.kf[SK_TWO_H + t1];
+            gtan[ta][f] = a0 * A.kf[SK_TWO_H + ta];
+            gtan[2][f] = a1 * A.kf[SK_TWO_H + 2];
         }
     }
     float Fh[NC];
     z3_face_flux<Q, AV, NS, a>(sl, sr, p0, p1, ut, gtan, Tg, A, Fh, bad);
     const float w = A.kf[SK_CAX + a] * tG[p0] * tG[p1];
 #pragma unroll
-    for (int f = 0; f < NC; ++f) out[f * ostride + p0 + Q * p1] = w * Fh[f];
+    for (int f = 0; f < NC; ++f) sFh[(f * NFXY + face) * G + k] = w * Fh[f];
 }
 
 template <int N, bool AV, bool NS, int TX, int TY>
@@ -229,7 +234,7 @@ __global__ void __launch_bounds__(256, 2) stage3z_kernel(const StageArgs A, cons
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *sm = reinterpret_cast<float *>(smem_raw);
-    float *sFh = sm + PL::OFF_FH, *sFz = sm + PL::OFF_FZ, *sWig = sm + PL::OFF_WIG;
+    float *sFh = sm + PL::OFF_FH, *sUt = sm + PL::OFF_UT, *sFz = sm + PL::OFF_FZ, *sWig = sm + PL::OFF_WIG;
     float *tB = sm + PL::OFF_TAB, *tDn = tB + PL::TAB, *tWd = tDn + PL::TAB, *tG = tWd + PL::TAB;
     float *tLm = tG + PL::TAB, *tLp = tLm + PL::TAB;
     int *sG = reinterpret_cast<int *>(sm + PL::NREAL);
@@ -419,15 +424,38 @@ __global__ void __launch_bounds__(256, 2) stage3z_kernel(const StageArgs A, cons
         }
     };
 
-    // the lane group's shuffle mask; Dn rows of the lane's indices (ly, lz) in xor order, read from the
-    // shared table where they are used (they are not kept live across the plane step)
-    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
-    auto dn_rows = [&](float (&d0)[Q], float (&d1)[Q]) {
+    // z-face between the lane group's cell in slot sl (below) and slot sr (above), at the face point
+    // (x, y) = (gl % Q, gl / Q), by all lanes of the group; the weighted flux goes to fz[f * TC * G + gl]
+    auto zface = [&](const float *sl, const float *sr, bool valid, float *fz) {
+        const int px = gl % Q, py = gl / Q;
+        float ut[NC];
+        float gtan[3][NC];
+        if (NS) {
+            if (sl && sr) z3_recover<Q, 2>(sl, sr, px, py, Tg, ut);
+            else {
 #pragma unroll
-        for (int k = 0; k < Q; ++k) {
-            d0[k] = tDn[ly * Q + (ly ^ k)];
-            d1[k] = tDn[lz * Q + (lz ^ k)];
+                for (int f = 0; f < NC; ++f) ut[f] = 0.0f;
+            }
+            // tangential derivatives of the recovered state: across the group's lanes (all lanes take part)
+            float dx[Q], dy[Q];
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                dx[k] = tDn[px * Q + (px ^ k)];
+                dy[k] = tDn[py * Q + (py ^ k)];
+            }
+#pragma unroll
+            for (int f = 0; f < NC; ++f) {
+                gtan[0][f] = xmatvec<Q, 1>(ut[f], dx) * K[SK_TWO_H + 0];
+                gtan[1][f] = xmatvec<Q, Q>(ut[f], dy) * K[SK_TWO_H + 1];
+                gtan[2][f] = 0.0f;
+            }
         }
+        if (!valid) return;
+        float Fh[NC];
+        z3_face_flux<Q, AV, NS, 2>(sl, sr, px, py, ut, gtan, Tg, A, Fh, bad);
+        const float w = K[SK_CAX + 2] * tG[px] * tG[py];
+#pragma unroll
+        for (int f = 0; f < NC; ++f) fz[f * TC * G + gl] = w * Fh[f];
     };
 
     // work items: (column, z-chunk); the chunk length comes with the arguments
@@ -467,12 +495,9 @@ __global__ void __launch_bounds__(256, 2) stage3z_kernel(const StageArgs A, cons
             load_cell(own(0) + grp * PL::SLOT, gOwn(0)[grp], A.fused != 0, sWig + grp);
             load_cell(own(1) + grp * PL::SLOT, gOwn(1)[grp], false, nullptr);
             __syncthreads();
-            if (mine) {
-                float dp0[Q], dp1[Q];
-                dn_rows(dp0, dp1);
-                z3_face_task<Q, AV, NS, 2>(zp >= 0 ? own(1) + grp * PL::SLOT : nullptr, own(0) + grp * PL::SLOT, ly,
-                                           lz, dp0, dp1, gmask, tG, Tg, A, sFz + NC * TC * G + grp * G, TC * G, bad);
-            }
+            const bool below = zp >= 0;
+            zface(below ? own(1) + grp * PL::SLOT : nullptr, own(0) + grp * PL::SLOT, mine,
+                  sFz + NC * TC * G + grp * G);
             __syncthreads();
         }
 
@@ -530,31 +555,56 @@ __global__ void __launch_bounds__(256, 2) stage3z_kernel(const StageArgs A, cons
                 else s = 2 * TY + TX + cx;
                 return gHalo[s] >= 0 ? halo + s * PL::SLOT : nullptr;
             };
-            // (F) every face of the plane step, one per lane group: the x- and y-faces of plane z (into
-            // sFh) and the z-faces between planes z and z + 1 (into sFz, buffer cur)
-            for (int t = grp; t < NFXY + TC; t += TC) {
-                float dp0[Q], dp1[Q];
-                dn_rows(dp0, dp1);
-                if (t < NFX) {
-                    const int px = t % (TX + 1), cy = t / (TX + 1);
-                    if (px > V0 || cy >= V1) continue;
-                    const float *sl = slot_at(px - 1, cy), *sr = slot_at(px, cy);
-                    if (!sl && !sr) continue;
-                    z3_face_task<Q, AV, NS, 0>(sl, sr, ly, lz, dp0, dp1, gmask, tG, Tg, A, sFh + t * G, NFXY * G, bad);
-                } else if (t < NFXY) {
-                    const int fy = t - NFX;
-                    const int cx = fy % TX, py = fy / TX;
-                    if (cx >= V0 || py > V1) continue;
-                    const float *sl = slot_at(cx, py - 1), *sr = slot_at(cx, py);
-                    if (!sl && !sr) continue;
-                    z3_face_task<Q, AV, NS, 1>(sl, sr, ly, lz, dp0, dp1, gmask, tG, Tg, A, sFh + t * G, NFXY * G, bad);
+            // decode x/y face point q: axis, the two sides, face index and point (p0, p1) in the face
+            auto face_of = [&](int q, int &a, const float *&sl, const float *&sr, int &face, int &p0, int &p1) -> bool {
+                face = q / G;
+                const int k = q % G;
+                p0 = k % Q;
+                p1 = k / Q;
+                if (face < NFX) {
+                    a = 0;
+                    const int px = face % (TX + 1), cy = face / (TX + 1);
+                    if (px > V0 || cy >= V1) return false;
+                    sl = slot_at(px - 1, cy);
+                    sr = slot_at(px, cy);
                 } else {
-                    const int c = t - NFXY;
-                    if (c % TX >= V0 || c / TX >= V1) continue;
-                    z3_face_task<Q, AV, NS, 2>(sCur + c * PL::SLOT, zn >= 0 ? sNxt + c * PL::SLOT : nullptr, ly, lz,
-                                               dp0, dp1, gmask, tG, Tg, A, sFz + cur * NC * TC * G + c * G, TC * G,
-                                               bad);
+                    a = 1;
+                    const int fy = face - NFX;
+                    const int cx = fy % TX, py = fy / TX;
+                    if (cx >= V0 || py > V1) return false;
+                    sl = slot_at(cx, py - 1);
+                    sr = slot_at(cx, py);
                 }
+                return sl || sr;
+            };
+
+            // (R) recovered state at the x/y face points; the top z-face of every own cell
+            if (NS) {
+                for (int q = tid; q < NFXY * G; q += NTH) {
+                    int a, face, p0, p1;
+                    const float *sl, *sr;
+                    if (!face_of(q, a, sl, sr, face, p0, p1) || !sl || !sr) continue;
+                    float ut[NC];
+                    if (a == 0) z3_recover<Q, 0>(sl, sr, p0, p1, Tg, ut);
+                    else z3_recover<Q, 1>(sl, sr, p0, p1, Tg, ut);
+#pragma unroll
+                    for (int f = 0; f < NC; ++f) sUt[(f * NFXY + face) * G + q % G] = ut[f];
+                }
+            }
+            zface(sCur + grp * PL::SLOT, zn >= 0 ? sNxt + grp * PL::SLOT : nullptr, mine,
+                  sFz + cur * NC * TC * G + grp * G);
+            __syncthreads();
+
+            // (F) x/y face fluxes, weighted for the lift (one code path per axis, the axis a
+            // compile-time constant)
+            for (int q = tid; q < NFXY * G; q += NTH) {
+                int a, face, p0, p1;
+                const float *sl, *sr;
+                if (!face_of(q, a, sl, sr, face, p0, p1)) continue;
+                if (a == 0)
+                    z3_xy_flux<Q, AV, NS, NFXY, 0>(sl, sr, face, p0, p1, q % G, sUt, tDn, tG, Tg, A, sFh, bad);
+                else
+                    z3_xy_flux<Q, AV, NS, NFXY, 1>(sl, sr, face, p0, p1, q % G, sUt, tDn, tG, Tg, A, sFh, bad);
             }
             __syncthreads();
 
@@ -566,10 +616,11 @@ __global__ void __launch_bounds__(256, 2) stage3z_kernel(const StageArgs A, cons
                 float u[NF][Q];
 #pragma unroll
                 for (int f = 0; f < NF; ++f) ld_line<Q, VEC>(slot + f * NP + z3_line<Q>(ly, lz), u[f]);
-                float dp0[Q], dp1[Q], wy[Q], wz[Q];
-                dn_rows(dp0, dp1);
+                float dy[Q], dz[Q], wy[Q], wz[Q];
 #pragma unroll
                 for (int k = 0; k < Q; ++k) {
+                    dy[k] = tDn[ly * Q + (ly ^ k)];
+                    dz[k] = tDn[lz * Q + (lz ^ k)];
                     wy[k] = tWd[ly * Q + (ly ^ k)];
                     wz[k] = tWd[lz * Q + (lz ^ k)];
                 }
@@ -594,8 +645,8 @@ __global__ void __launch_bounds__(256, 2) stage3z_kernel(const StageArgs A, cons
 #pragma unroll
                             for (int m = 0; m < Q; ++m) acc = fmaf(Tg.Dn[x][m], u[f][m], acc);
                             gr[0][f] = acc * K[SK_TWO_H + 0];
-                            gr[1][f] = xmatvec<Q, 1>(u[f][x], dp0) * K[SK_TWO_H + 1];
-                            gr[2][f] = xmatvec<Q, Q>(u[f][x], dp1) * K[SK_TWO_H + 2];
+                            gr[1][f] = xmatvec<Q, 1>(u[f][x], dy) * K[SK_TWO_H + 1];
+                            gr[2][f] = xmatvec<Q, Q>(u[f][x], dz) * K[SK_TWO_H + 2];
                         }
                     }
                     float rho, v[3], p, cs;
