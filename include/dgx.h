@@ -105,9 +105,12 @@ typedef struct dg_grid {
  *             every l_a <= n, (n+1)^d modes; DG_BASIS_TOTAL: the paper's
  *             truncation l_x + l_y + l_z <= n (Sec. 2.3; (n+1)(n+2)/2 modes in
  *             2-D, (n+1)(n+2)(n+3)/6 in 3-D), in the same order with the other
- *             modes left out.  States passed in and out hold those modes only;
- *             the library keeps them in the tensor layout with the others at
- *             zero (the same arithmetic per step; no memory saving).  The
+ *             modes left out.  States passed in and out hold those modes only.
+ *             3-D FP32-bulk handles of degree 1 or 3 without a tracer store
+ *             only those modes on the device too ((n+1)(n+2)(n+3)/6 instead
+ *             of (n+1)^3 values per cell and field; such handles cannot join
+ *             a batch); the others keep the tensor layout with the other modes
+ *             at zero.  The arithmetic per step is the tensor arithmetic.  The
  *             oscillation sensor's high modes become l_x + l_y + l_z = n.
  *             Changing it reallocates the state.  dg_max_dt_noalloc reads
  *             tensor-layout states only. */

@@ -236,6 +236,12 @@ struct dg_handle {
 
     // total-degree basis (Sec. 2.3): modes seen by the caller, their tensor indices, staging buffer
     int Mapi = 1;
+    // packed total-degree storage: the state arrays hold only the Mapi basis modes per cell (used where
+    // the stage kernel reads and writes it: 3-D FP32-bulk, degrees 1 and 3, no tracer); Ms = stored
+    // modes per cell, d_cmap[l] = stored index of tensor mode l or -1
+    int packed = 0;
+    int Ms = 1;
+    int *d_cmap = nullptr;
     int *d_modemap = nullptr;
     double *stage = nullptr;  // [fields][cells][Mapi] for host transfers
 
@@ -298,12 +304,16 @@ void free_buffers(dg_t *h)
     h->fstate = h->smodes = nullptr;
     h->force = h->ftab = nullptr;
     cudaFree(h->d_modemap);
+    cudaFree(h->d_cmap);
     cudaFree(h->stage);
     h->d_modemap = nullptr;
+    h->d_cmap = nullptr;
     h->stage = nullptr;
 }
 
 bool total_degree(const dg_t *h) { return h->p.basis == DG_BASIS_TOTAL; }
+// the caller's total-degree layout differs from the stored one (tensor storage with zeros)
+bool expands(const dg_t *h) { return total_degree(h) && !h->packed; }
 size_t nw_api(const dg_t *h) { return (size_t)h->nf * h->ncell * h->Mapi; }
 
 int expand_state(dg_t *h, const double *src, double *dst)
@@ -386,7 +396,19 @@ int alloc_buffers(dg_t *h)
     free_buffers(h);
     h->nc = h->dim + 2 + (h->p.tracer_on ? 1 : 0);
     h->nf = h->nc + (h->p.av_on ? 1 : 0);
-    h->nw = (size_t)h->nf * h->ncell * h->M;
+    // modes seen by the caller: all tensor modes, or those with l_x + l_y + l_z <= n
+    std::vector<int> modemap, cmap(h->M, -1);
+    for (int t = 0; t < h->M; ++t) {
+        const int lx = t % h->Q, ly = (t / h->Q) % h->Q, lz = h->dim == 3 ? t / (h->Q * h->Q) : 0;
+        if (h->p.basis != DG_BASIS_TOTAL || lx + ly + lz <= h->degree) {
+            cmap[t] = (int)modemap.size();
+            modemap.push_back(t);
+        }
+    }
+    h->Mapi = (int)modemap.size();
+    h->packed = total_degree(h) && h->dim == 3 && fp32(h) && (h->degree == 1 || h->degree == 3) && !h->p.tracer_on;
+    h->Ms = h->packed ? h->Mapi : h->M;
+    h->nw = (size_t)h->nf * h->ncell * h->Ms;
     const size_t rs = real_size(h);
     const int fail_at = injected_alloc_failure();
     int nalloc = 0;
@@ -428,14 +450,12 @@ int alloc_buffers(dg_t *h)
     if (!st) st = al((void **)&h->partial, 2 * (size_t)h->partial_cap * sizeof(double));
     if (!st) st = al((void **)&h->sums, ((size_t)kSumBlocks * h->nc + h->nc) * sizeof(double));
     if (!st) st = al((void **)&h->status, sizeof(int));
-    // modes seen by the caller: all tensor modes, or those with l_x + l_y + l_z <= n
-    std::vector<int> modemap;
-    for (int t = 0; t < h->M; ++t) {
-        const int lx = t % h->Q, ly = (t / h->Q) % h->Q, lz = h->dim == 3 ? t / (h->Q * h->Q) : 0;
-        if (h->p.basis != DG_BASIS_TOTAL || lx + ly + lz <= h->degree) modemap.push_back(t);
+    if (!st && h->packed) {
+        st = al((void **)&h->d_cmap, cmap.size() * sizeof(int));
+        if (!st && cudaMemcpy(h->d_cmap, cmap.data(), cmap.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+            st = fail(h, DG_ECUDA, "mode map upload");
     }
-    h->Mapi = (int)modemap.size();
-    if (!st && total_degree(h)) {
+    if (!st && total_degree(h) && !h->packed) {
         st = al((void **)&h->d_modemap, modemap.size() * sizeof(int));
         if (!st) st = al((void **)&h->stage, nw_api(h) * sizeof(double));
         if (!st && cudaMemcpy(h->d_modemap, modemap.data(), modemap.size() * sizeof(int), cudaMemcpyHostToDevice) !=
@@ -481,6 +501,8 @@ void base_stage_args(const dg_t *h, StageArgs &a)
     a.tracer_on = h->p.tracer_on;
     a.eta = h->p.tracer_eta;
     a.total_degree = total_degree(h) ? 1 : 0;
+    a.cmap = h->packed ? h->d_cmap : nullptr;
+    a.ms = h->Ms;
     a.av_on = h->p.av_on;
     a.av_scale = h->p.av_scale;
     a.f_v = h->p.f_v;
@@ -525,6 +547,8 @@ cudaError_t launch_prologue_any(const dg_t *h, int update_sensor)
     a.partial = h->partial;
     a.status = h->status;
     a.total_degree = total_degree(h) ? 1 : 0;
+    a.cmap = h->packed ? h->d_cmap : nullptr;
+    a.ms = h->Ms;
     if (h->dim == 2)
         return fp32(h) ? launch_prologue_2d_f32(h->degree, a, h->tf, h->stream)
                        : launch_prologue_2d_f64(h->degree, a, h->td, h->stream);
@@ -617,6 +641,8 @@ LimiterArgs entry_limiter_args(const dg_t *h)
     la.ufull = h->U[h->cur];
     la.uhi = fp32(h) ? h->Uhi[h->cur] : nullptr;
     la.status = h->status;
+    la.cmap = h->packed ? h->d_cmap : nullptr;
+    la.ms = h->Ms;
     return la;
 }
 
@@ -636,6 +662,8 @@ LimiterArgs stage_limiter_args(const dg_t *h, const Schedule &S, int i, int c)
     la.ufull = d.last ? h->U[nx] : nullptr;
     la.uhi = d.last && fp32(h) ? h->Uhi[nx] : nullptr;
     la.status = h->status;
+    la.cmap = h->packed ? h->d_cmap : nullptr;
+    la.ms = h->Ms;
     return la;
 }
 
@@ -926,7 +954,7 @@ int dg_set_stream(dg_t *h, void *stream)
 int dg_set_state(dg_t *h, const double *host_w)
 {
     if (!h || !host_w) return DG_EINVAL;
-    if (total_degree(h)) {
+    if (expands(h)) {
         CK(h, cudaMemcpyAsync(h->stage, host_w, nw_api(h) * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         int st = expand_state(h, h->stage, h->U[h->cur]);
         if (st) return st;
@@ -942,7 +970,7 @@ int dg_set_state(dg_t *h, const double *host_w)
 int dg_set_state_device(dg_t *h, const double *dev_w)
 {
     if (!h || !dev_w) return DG_EINVAL;
-    if (total_degree(h)) {
+    if (expands(h)) {
         int st = expand_state(h, dev_w, h->U[h->cur]);
         if (st) return st;
     } else {
@@ -954,7 +982,7 @@ int dg_set_state_device(dg_t *h, const double *dev_w)
 int dg_get_state(dg_t *h, double *host_w)
 {
     if (!h || !host_w) return DG_EINVAL;
-    if (total_degree(h)) {
+    if (expands(h)) {
         int st = compact_state(h, h->U[h->cur], h->stage);
         if (st) return st;
         CK(h, cudaMemcpyAsync(host_w, h->stage, nw_api(h) * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -967,7 +995,7 @@ int dg_get_state(dg_t *h, double *host_w)
 int dg_get_state_device(dg_t *h, double *dev_w)
 {
     if (!h || !dev_w) return DG_EINVAL;
-    if (total_degree(h)) return compact_state(h, h->U[h->cur], dev_w);
+    if (expands(h)) return compact_state(h, h->U[h->cur], dev_w);
     CK(h, cudaMemcpyAsync(dev_w, h->U[h->cur], h->nw * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     return DG_OK;
 }
@@ -976,7 +1004,7 @@ int dg_get_state_device(dg_t *h, double *dev_w)
 int dg_rhs_device(dg_t *h, double *dev_out)
 {
     if (!h || !dev_out) return DG_EINVAL;
-    if (!total_degree(h)) return rhs_tensor(h, dev_out);
+    if (!expands(h)) return rhs_tensor(h, dev_out);
     int st = ensure_rhs_tmp(h);
     if (!st) st = rhs_tensor(h, h->rhs_tmp);
     if (!st) st = compact_state(h, h->rhs_tmp, dev_out);
@@ -989,7 +1017,7 @@ int dg_rhs(dg_t *h, double *host_out)
     int st = ensure_rhs_tmp(h);
     if (!st) st = rhs_tensor(h, h->rhs_tmp);
     if (st) return st;
-    if (total_degree(h)) {
+    if (expands(h)) {
         st = compact_state(h, h->rhs_tmp, h->stage);
         if (st) return st;
         CK(h, cudaMemcpyAsync(host_out, h->stage, nw_api(h) * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -1103,7 +1131,7 @@ int dg_conserved_sums(dg_t *h, double *out)
     if (!h || !out) return DG_EINVAL;
     double vol = 1.0;
     for (int a = 0; a < h->dim; ++a) vol *= h->h[a];
-    sums_kernel<<<kSumBlocks, 256, 0, h->stream>>>(h->U[h->cur], h->ncell, h->M, h->nc, h->sums);
+    sums_kernel<<<kSumBlocks, 256, 0, h->stream>>>(h->U[h->cur], h->ncell, h->Ms, h->nc, h->sums);
     sums_final_kernel<<<1, 32, 0, h->stream>>>(h->sums, kSumBlocks, h->nc, vol, h->sums + kSumBlocks * h->nc);
     CK(h, cudaGetLastError());
     CK(h, cudaMemcpyAsync(out, h->sums + kSumBlocks * h->nc, h->nc * sizeof(double), cudaMemcpyDeviceToHost,
@@ -1281,7 +1309,9 @@ int dg_batch_create(dg_t *const *sims, int count, dg_batch_t **out)
     for (int k = 0; k < count; ++k) {
         const dg_t *h = sims[k];
         if (!h) return DG_EINVAL;
-        if (h->p.forcing_on || h->p.tracer_on || stage_count(h) < 2) return DG_EUNSUPPORTED;
+        // driving and tracer members, and members in packed total-degree storage (the batched kernel
+        // reads tensor storage), are not batched
+        if (h->p.forcing_on || h->p.tracer_on || h->packed || stage_count(h) < 2) return DG_EUNSUPPORTED;
         if (h->cur != sims[0]->cur || h->device != sims[0]->device || h->stream != sims[0]->stream)
             return DG_EINVAL;
     }

@@ -107,6 +107,10 @@ struct StageArgs {
     int tracer_on;  // passive tracer field rho c after the energy (Sec. 3.4)
     double eta;     // its diffusivity
     int total_degree;  // basis of modes l_x + l_y + l_z <= n (Sec. 2.3): the others are kept at zero
+    // packed total-degree storage: the state arrays hold ms modes per cell, the total-degree modes
+    // in tensor order; cmap[l] = stored index of tensor mode l, or -1 (null: tensor storage, ms = NP)
+    const int *cmap;
+    int ms;
     int av_on;
     double av_scale, f_v, f_tau;
     int nf;  // fields incl. alpha
@@ -204,6 +208,8 @@ struct PrologueArgs {
     double *partial;  // [blocks][2] max c_s, max |v|
     int *status;
     int total_degree;  // sensor: high modes are l_x + l_y + l_z = n instead of some l_a = n
+    const int *cmap;   // packed total-degree storage (see StageArgs::cmap), or null
+    int ms;            // stored modes per cell
 };
 
 // Arguments of the positivity-limiter kernel (Sec. 4.2), run after a stage.
@@ -217,6 +223,8 @@ struct LimiterArgs {
     float *uhi;          // FP32 copy of ufull to refresh (bulk mode, last stage) or null
     int *status;
     int tracer_on;       // a passive tracer follows the energy: d+3 conserved fields are scaled
+    const int *cmap;     // packed total-degree storage (see StageArgs::cmap), or null
+    int ms;              // stored modes per cell
 };
 
 struct LaunchCfg {

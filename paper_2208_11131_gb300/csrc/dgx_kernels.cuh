@@ -357,7 +357,10 @@ __global__ void __launch_bounds__(256) prologue_kernel(const PrologueArgs A, con
         const int l = idx % NP, fc = idx / NP;
         const int c = fc % TC, f = fc / TC;
         const int g = sG[c];
-        sU[idx] = g >= 0 ? u[((size_t)f * A.ncell + g) * NP + l] : Real(0);
+        // packed total-degree storage: the modes outside the basis are not stored (zero)
+        const int sl = A.cmap ? A.cmap[l] : l;
+        const int ms = A.cmap ? A.ms : NP;
+        sU[idx] = (g >= 0 && sl >= 0) ? u[((size_t)f * A.ncell + g) * ms + sl] : Real(0);
     }
     __syncthreads();
     if (A.update_sensor) {

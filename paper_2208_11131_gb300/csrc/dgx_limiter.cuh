@@ -59,9 +59,16 @@ __global__ void limiter_kernel(const LimiterArgs A, const Tables<Real> Tg)
     if (cell >= A.ncell) return;
     const Real *ub = static_cast<const Real *>(A.ubase);
     Real *dl = static_cast<Real *>(A.delta);
+    // packed total-degree storage: cmap gives the stored index of a tensor mode (-1: not stored, zero)
+    const int ms = A.cmap ? A.ms : NP;
     for (int i = lane; i < NC * NP; i += 32) {
         const int f = i / NP, l = i % NP;
-        const size_t gi = ((size_t)f * A.ncell + cell) * NP + l;
+        const int sl = A.cmap ? A.cmap[l] : l;
+        if (sl < 0) {
+            sM[i] = Real(0);
+            continue;
+        }
+        const size_t gi = ((size_t)f * A.ncell + cell) * ms + sl;
         sM[i] = A.last ? (Real)A.ufull[gi] : ub[gi] + dl[gi];
     }
     __syncwarp();
@@ -163,8 +170,9 @@ __global__ void limiter_kernel(const LimiterArgs A, const Tables<Real> Tg)
     const Real sc = ldexp(theta, -kmax);
     for (int i = lane; i < NC * NP; i += 32) {
         const int f = i / NP, l = i % NP;
-        if (l == 0) continue;
-        const size_t gi = ((size_t)f * A.ncell + cell) * NP + l;
+        const int sl = A.cmap ? A.cmap[l] : l;
+        if (l == 0 || sl < 0) continue;
+        const size_t gi = ((size_t)f * A.ncell + cell) * ms + sl;
         if (A.last) {
             const double u = A.ufull[gi] * (double)sc;
             A.ufull[gi] = u;

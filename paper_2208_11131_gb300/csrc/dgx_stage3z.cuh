@@ -223,6 +223,31 @@ __device__ __forceinline__ void z3_xy_flux(const float *sl, const float *sr, int
     for (int f = 0; f < NC; ++f) sFh[(f * NFXY + face) * G + k] = w * Fh[f];
 }
 
+// One modal x-line of a global state array: Q values with the widest aligned vector accesses, or, in
+// packed total-degree storage, the line's len stored modes (scalar; the others read as zero, are not
+// written)
+template <int Q, int VEC, typename T>
+__device__ __forceinline__ void z3_ld(const T *p, bool packed, int len, T (&w)[Q])
+{
+    if (!packed) {
+        ld_line<Q, VEC>(p, w);
+        return;
+    }
+#pragma unroll
+    for (int m = 0; m < Q; ++m) w[m] = m < len ? p[m] : T(0);
+}
+template <int Q, int VEC, typename T>
+__device__ __forceinline__ void z3_st(T *p, bool packed, int len, const T (&w)[Q])
+{
+    if (!packed) {
+        st_line<Q, VEC>(p, w);
+        return;
+    }
+#pragma unroll
+    for (int m = 0; m < Q; ++m)
+        if (m < len) p[m] = w[m];
+}
+
 template <int N, bool AV, bool NS, int TX, int TY>
 __global__ void __launch_bounds__(256, 2) stage3z_kernel(const StageArgs A, const Tables<float> Tg)
 {
@@ -307,7 +332,13 @@ __global__ void __launch_bounds__(256, 2) stage3z_kernel(const StageArgs A, cons
     float *dout = static_cast<float *>(A.dout);
     const bool readx = xb && (A.cx != 0.0 || A.zx != 0.0);
     const int N0 = A.N[0], N1 = A.N[1], N2 = A.N[2];
-    const size_t fstride = (size_t)A.ncell * NP;  // values between fields
+    // stored modes per cell, and the lane's modal x-line (l_y, l_z) = (ly, lz) in the global arrays:
+    // tensor storage, or packed total-degree storage (the line's modes l_x <= n - l_y - l_z)
+    const bool packed = A.cmap != nullptr;
+    const int MS = packed ? A.ms : NP;
+    const int plen = packed ? max(0, N + 1 - ly - lz) : Q;
+    const int poff = packed ? (plen > 0 ? A.cmap[Q * (ly + Q * lz)] : 0) : gl * Q;
+    const size_t fstride = (size_t)A.ncell * MS;  // values between fields
 
     float cmax = 0.0f, vmax = 0.0f;  // CFL speeds (fused first stage)
     int bad = 0;
@@ -342,14 +373,14 @@ __global__ void __launch_bounds__(256, 2) stage3z_kernel(const StageArgs A, cons
         const bool valid = g >= 0;
         float w[NF][Q];
         if (valid) {
-            const size_t g0 = (size_t)g * NP + (size_t)gl * Q;
+            const size_t g0 = (size_t)g * MS + (size_t)poff;
 #pragma unroll
-            for (int f = 0; f < NF; ++f) ld_line<Q, VEC>(ub + g0 + f * fstride, w[f]);
+            for (int f = 0; f < NF; ++f) z3_ld<Q, VEC>(ub + g0 + f * fstride, packed, plen, w[f]);
             if (di) {
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
                     float dd[Q];
-                    ld_line<Q, VEC>(di + g0 + f * fstride, dd);
+                    z3_ld<Q, VEC>(di + g0 + f * fstride, packed, plen, dd);
 #pragma unroll
                     for (int m = 0; m < Q; ++m) w[f][m] = w[f][m] + dsc * dd[m];
                 }
@@ -752,10 +783,10 @@ __global__ void __launch_bounds__(256, 2) stage3z_kernel(const StageArgs A, cons
                     // epilogue on the modal x-line (l_y, l_z) = (ly, lz)
 #pragma unroll
                     for (int f = 0; f < NF; ++f) {
-                        const size_t gi = (size_t)f * fstride + (size_t)g * NP + (size_t)gl * Q;
+                        const size_t gi = (size_t)f * fstride + (size_t)g * MS + (size_t)poff;
                         constexpr int VD = (Q * 8) % 16 == 0 ? 16 : 8;
                         double uo[Q];
-                        if (A.mode == 2) ld_line<Q, VD>(A.uold + gi, uo);
+                        if (A.mode == 2) z3_ld<Q, VD>(A.uold + gi, packed, plen, uo);
                         float L[Q];
 #pragma unroll
                         for (int l = 0; l < Q; ++l) {
@@ -771,12 +802,13 @@ __global__ void __launch_bounds__(256, 2) stage3z_kernel(const StageArgs A, cons
                         }
                         if (A.mode == 0) {
 #pragma unroll
-                            for (int l = 0; l < Q; ++l) A.rhs_out[gi + l] = (double)L[l];
+                            for (int l = 0; l < Q; ++l)
+                                if (l < plen) A.rhs_out[gi + l] = (double)L[l];
                             continue;
                         }
                         float din[Q], xv[Q], dnew[Q], zn_[Q];
                         if (di) {
-                            ld_line<Q, VEC>(di + gi, din);
+                            z3_ld<Q, VEC>(di + gi, packed, plen, din);
 #pragma unroll
                             for (int l = 0; l < Q; ++l) din[l] = dsc * din[l];
                         } else {
@@ -784,7 +816,7 @@ __global__ void __launch_bounds__(256, 2) stage3z_kernel(const StageArgs A, cons
                             for (int l = 0; l < Q; ++l) din[l] = 0.0f;
                         }
                         if (readx) {
-                            ld_line<Q, VEC>(xb + gi, xv);
+                            z3_ld<Q, VEC>(xb + gi, packed, plen, xv);
                         } else {
 #pragma unroll
                             for (int l = 0; l < Q; ++l) xv[l] = 0.0f;
@@ -795,19 +827,19 @@ __global__ void __launch_bounds__(256, 2) stage3z_kernel(const StageArgs A, cons
                             dnew[l] = ca * din[l] + cxc * xv[l] + cb * dtL;
                             zn_[l] = za * din[l] + zx * xv[l] + zb * dtL;
                         }
-                        if (A.write_z) st_line<Q, VEC>(xb + gi, zn_);
+                        if (A.write_z) z3_st<Q, VEC>(xb + gi, packed, plen, zn_);
                         if (A.mode == 1) {
-                            st_line<Q, VEC>(dout + gi, dnew);
+                            z3_st<Q, VEC>(dout + gi, packed, plen, dnew);
                         } else {
                             double un[Q];
 #pragma unroll
                             for (int l = 0; l < Q; ++l) un[l] = uo[l] + (double)dnew[l];
-                            st_line<Q, VD>(A.unew + gi, un);
+                            z3_st<Q, VD>(A.unew + gi, packed, plen, un);
                             if (A.uhi_new) {
                                 float uf[Q];
 #pragma unroll
                                 for (int l = 0; l < Q; ++l) uf[l] = (float)un[l];
-                                st_line<Q, VEC>(A.uhi_new + gi, uf);
+                                z3_st<Q, VEC>(A.uhi_new + gi, packed, plen, uf);
                             }
                         }
                     }

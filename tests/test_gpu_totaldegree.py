@@ -133,3 +133,79 @@ def test_total_degree_batched_members():
     dgx.dg_batch_destroy(batch)
     for s in a + b:
         s.close()
+
+
+# 3-D FP32-bulk at degrees 1 and 3 (no tracer) stores only the total-degree modes (packed storage:
+# (n+1)(n+2)(n+3)/6 of (n+1)^3 values per cell and field); the stage, prologue and limiter kernels
+# read and write that layout directly.
+PACKED = [
+    (3, (9, 6, 7), 1e-3, 1, 0),
+    (3, (5, 4, 9), 0.0, 1, 1),
+    (1, (10, 9, 6), 1e-3, 1, 0),
+    (3, (6, 5, 4), 0.0, 0, 0),
+]
+
+
+@pytest.mark.parametrize("n,N,nu,av,lim", PACKED)
+def test_packed_total_degree_rhs_and_steps(n, N, nu, av, lim, monkeypatch):
+    monkeypatch.setenv("DGX_ZCHUNK", "3")  # multi-plane chunks of the z-marching kernel
+    wl = _wl(3, n, N, (1.0, 0.9, 1.1), nu, av, 0, lim, bc=(1, 0, 0) if lim else (0, 0, 0))
+    P = problem(wl)
+    if lim:
+        w = inputs.project(wl, inputs.sod_tube_ic(wl))
+    else:
+        w = inputs.random_modal_state(wl, seed=80 + n)
+    ref, st = oracle.rhs(P, w)
+    assert st == 0
+    sim = dgx.Simulation(wl, precision=dgx.DG_FP32_BULK)
+    assert sim.M == P.M == len(inputs.mode_exponents(3, n, 1))
+    sim.set_state(w)
+    assert np.array_equal(sim.get_state(), w)
+    assert rhs_err(sim.rhs(), ref, P, w) < 1e-5
+    o = oracle.Sim(P, w)
+    for _ in range(4):
+        _, st = o.step()
+        assert st == 0
+        sim.step()
+    assert rel_l1(sim.get_state(), o.w, 0) < 1e-5
+    assert abs(sim.max_dt() / oracle.max_dt(P, o.w)[0] - 1) < 1e-5
+    wg = sim.get_state()  # the sums read the cell means at the packed stride
+    assert np.allclose(sim.conserved_sums(), [np.sum(wg[f, :, 0]) * np.prod(P.h) for f in range(5)], rtol=1e-12,
+                       atol=1e-14)
+    sim.close()
+
+
+def test_packed_total_degree_state_is_the_basis_size():
+    """device memory of a 3-D degree-3 FP32-bulk handle: total-degree storage holds 20 of the 64
+    tensor modes per cell and field"""
+    torch = pytest.importorskip("torch")
+    wl = _wl(3, 3, (32, 32, 32), (1.0, 1.0, 1.0), 1e-3, 1)
+    used = {}
+    for basis in (0, 1):
+        torch.cuda.synchronize()
+        f0, _ = torch.cuda.mem_get_info()
+        sim = dgx.Simulation(wl.with_(basis=basis), precision=dgx.DG_FP32_BULK)
+        torch.cuda.synchronize()
+        f1, _ = torch.cuda.mem_get_info()
+        used[basis] = f0 - f1
+        sim.close()
+    state = 6 * 32 ** 3 * (8 + 8 + 4 + 4 + 3 * 4)  # bytes per state value: u^n, u^n+1, FP32 copies, 3 deltas
+    assert used[0] >= 64 * state
+    assert used[1] < 0.34 * used[0]  # 20/64 = 0.3125 plus the per-handle scalars
+
+
+def test_packed_total_degree_device_transfers_and_batch_refusal():
+    torch = pytest.importorskip("torch")
+    wl = _wl(3, 3, (5, 4, 3), (1.0, 1.0, 1.0), 1e-3, 1)
+    w = inputs.random_modal_state(wl, seed=5)
+    sim = dgx.Simulation(wl, precision=dgx.DG_FP32_BULK)
+    dw = torch.from_numpy(w).cuda()
+    dgx.dg_set_state_device(sim.h, dw.data_ptr())
+    back = torch.zeros_like(dw)
+    dgx.dg_get_state_device(sim.h, back.data_ptr())
+    torch.cuda.synchronize()
+    assert torch.equal(back, dw)
+    with pytest.raises(dgx.DGError) as e:
+        dgx.dg_batch_create([sim.h])
+    assert e.value.code == dgx.DG_EUNSUPPORTED
+    sim.close()
