@@ -647,6 +647,14 @@ def dgx_arm(args, rank, ws, local):
         if rank == 0 and ws == 1:
             line["cpu_baseline"] = cpu_baseline(args.workload)
     sim.close()
+    if not args.no_extras and default:
+        # the paper's total-degree basis on the same box (Sec. 2.3): the headline's initial state
+        # restricted to the modes l_x + l_y + l_z <= n, stored packed (20 of 64 modes per cell)
+        wlt = wl.with_(basis=1)
+        keep = [i for i, e in enumerate(inputs.mode_exponents(3, wl.n, 0)) if e.sum() <= wl.n]
+        per, st = timed_steps(dgx, wlt, np.ascontiguousarray(w0[:, :, keep]), 6, 2, stream, flush)
+        st.close()
+        line["total_degree_basis"] = path_line(wlt, per, label + "_total_degree_basis", True, peak)
     if not args.no_ensemble and default:
         line["ensemble"] = ensemble_measurement(dgx, inputs, torch, stream, steps=20, warmup=3)
         # where batching pays: 64 members of 32^2 to 128^2 cells, each too small to fill the GPU alone

@@ -73,6 +73,56 @@ __global__ void limiter_kernel(const LimiterArgs A, const Tables<Real> Tg)
     }
     __syncwarp();
 
+    // A test from the modes alone.  On the reference cell |phi_l| <= c_l = prod_a sqrt(2 l_a + 1), so
+    // every point value of field f lies within w_0 +- V_f, V_f = sum_{l>0} c_l |w_l|.  If the density
+    // and pressure lower bounds of those intervals clear rho_bottom and p_bottom by a margin far above
+    // the rounding of the point evaluation, the evaluation below would find theta = 1 and no halving
+    // at every point -- the case in which it leaves the cell as it is -- so the cell is left now.
+    {
+        const Real gam = (Real)A.gamma;
+        Real var[NC];
+#pragma unroll
+        for (int f = 0; f < NC; ++f) var[f] = Real(0);
+        for (int l = 1 + lane; l < NP; l += 32) {
+            const int l0 = l % Q, l1 = (l / Q) % Q, l2 = DIM == 3 ? l / (Q * Q) : 0;
+            const Real c = sqrt(Real((2 * l0 + 1) * (2 * l1 + 1) * (2 * l2 + 1)));
+#pragma unroll
+            for (int f = 0; f < NC; ++f) var[f] += c * fabs(sM[f * NP + l]);
+        }
+#pragma unroll
+        for (int f = 0; f < NC; ++f)
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) var[f] += __shfl_xor_sync(0xffffffffu, var[f], off);
+        Real m[NC];
+#pragma unroll
+        for (int f = 0; f < NC; ++f) m[f] = sM[f * NP];
+        const Real rho_lo = m[0] - var[0];
+        Real mom2 = Real(0);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            const Real mh = fabs(m[1 + a]) + var[1 + a];
+            mom2 += mh * mh;
+        }
+        const Real e_lo = m[DIM + 1] - var[DIM + 1];
+        // floors of Sec. 4.2 from the mean state (as below), and the margins
+        const Real ke_bar = [&] {
+            Real k = Real(0);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) k += m[1 + a] * m[1 + a];
+            return k;
+        }();
+        const Real p_bar = (gam - Real(1)) * (m[DIM + 1] - Real(0.5) * ke_bar / m[0]);
+        const Real tol = Real(1e-4);
+        bool keep = m[0] > Real(0) && rho_lo - Real(1e-6) * m[0] > tol * (fabs(m[0]) + var[0]);
+        if (keep) {
+            const Real kin = Real(0.5) * mom2 / rho_lo;
+            const Real p_lo = (gam - Real(1)) * (e_lo - kin);
+            keep = p_lo - Real(1e-6) * p_bar > tol * (gam - Real(1)) * (fabs(m[DIM + 1]) + var[DIM + 1] + kin);
+        }
+        // the lanes' butterfly sums may differ in the last bit: lane 0 decides for the warp
+        if (__shfl_sync(0xffffffffu, keep ? 1 : 0, 0)) return;
+    }
+
     // widen axis 0, then 1 (then 2): Q -> E values per line
     {
         // pass x: sM [Q^d] -> sA [E * Q^(d-1)]
