@@ -42,7 +42,8 @@ METRIC = "DOF-updates/s per GB300 (FP32-bulk vs FP64, same L1 error) + % HBM roo
 UNIT = "DOF-updates/s"
 FLUSH_BYTES = 256 << 20
 KERNEL_SRCS = [os.path.join(ROOT, "paper_2208_11131_gb300", "csrc", f)
-               for f in ("dgx_kernels.cuh", "dgx_stage2.cuh", "dgx_inst.cuh", "dgx_inst_2d_f32.cu", "dgx_inst_3d_f32.cu")]
+               for f in ("dgx_internal.h", "dgx_kernels.cuh", "dgx_stage2.cuh", "dgx_stage3z.cuh", "dgx_limiter.cuh",
+                         "dgx_inst.cuh", "dgx_inst_2d_f32.cu", "dgx_inst_3d_f32.cu", "dgx_inst_3d_packed_f32.cu", "dgx_inst_3d_f64.cu")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
 
 
@@ -182,6 +183,18 @@ def code_only(src: str) -> str:
     src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
     src = re.sub(r"//[^\n]*", " ", src)
     return " ".join(src.split())
+
+
+def counted_for(key: str, field: str):
+    """a per-launch figure (`field`) of a committed ncu summary, if the kernel source is unchanged"""
+    try:
+        tab = json.load(open(TRAFFIC_FILE))
+    except (OSError, ValueError):
+        return None
+    ent = tab.get(key)
+    if not ent or ent.get("kernel_sha256") != kernel_sha():
+        return None
+    return ent.get(field)
 
 
 def traffic_for(key: str):
@@ -640,6 +653,19 @@ def dgx_arm(args, rank, ws, local):
         line["other_precision"] = {"dtype": "f64" if fp32 else "f32", "ms_per_step": other_ms,
                                    "value": wl.dofs * 5 / (other_ms / 1e3), "unit": UNIT,
                                    "steps": nsteps_cmp - 2}
+        if fp32:
+            # the FP64 path is bound by the FP64 arithmetic rate: executed FP64 flops per stage launch
+            # (ncu: 2 x DFMA + DMUL + DADD thread instructions of the same kernel on this workload, per
+            # cell, scaled to the grid) over the measured stage-launch time, against the FP64 FMA peak
+            per_cell = counted_for(f"stage_kernel|{label}|fp64", "fp64_flops_per_cell")
+            st64 = float(np.mean([sum(x[2:]) for x in [dgx.dg_step_timed(other.h, 0.0, nl) for _ in range(2)]]))
+            pk = (alu_peaks() or {}).get("fp64_tflops")
+            if per_cell and pk:
+                ach = per_cell * wl.ncell * 5 / (st64 / 1e3) / 1e12
+                line["other_precision"]["alu_roofline"] = {
+                    "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                    "peak_source": "measured FP64 FMA chains (bench alu_peaks)",
+                    "flops_per_cell_per_launch": per_cell}
         line[f"fp32_vs_fp64_rel_l1_rho_after_{nsteps_cmp}_steps"] = l1
         other.close()
         ref.close()

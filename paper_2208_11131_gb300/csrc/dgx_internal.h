@@ -253,6 +253,8 @@ cudaError_t launch_limiter_2d_f64(int degree, const LimiterArgs &a, const Tables
 cudaError_t launch_limiter_2d_f32(int degree, const LimiterArgs &a, const Tables<float> &t, cudaStream_t s);
 cudaError_t launch_limiter_3d_f64(int degree, const LimiterArgs &a, const Tables<double> &t, cudaStream_t s);
 cudaError_t launch_limiter_3d_f32(int degree, const LimiterArgs &a, const Tables<float> &t, cudaStream_t s);
+// z-marching 3-D FP32-bulk stage kernel over packed total-degree storage (degrees 1 and 3)
+cudaError_t launch_stage3z_packed(int degree, const StageArgs &a, const Tables<float> &t, cudaStream_t s, int *grid);
 cudaError_t launch_stage_batch_2d_f64(int degree, int av, int ns, const StageArgs *descs, const int *tile_off,
                                       int nsims, int total, const Tables<double> &t, cudaStream_t s);
 cudaError_t launch_stage_batch_2d_f32(int degree, int av, int ns, const StageArgs *descs, const int *tile_off,

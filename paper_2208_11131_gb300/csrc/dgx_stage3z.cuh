@@ -229,7 +229,7 @@ __device__ __forceinline__ void z3_xy_flux(const float *sl, const float *sr, int
 template <int Q, int VEC, typename T>
 __device__ __forceinline__ void z3_ld(const T *p, bool packed, int len, T (&w)[Q])
 {
-    if (!packed) {
+    if (!packed) {  // (packed is a compile-time constant at every call)
         ld_line<Q, VEC>(p, w);
         return;
     }
@@ -248,7 +248,7 @@ __device__ __forceinline__ void z3_st(T *p, bool packed, int len, const T (&w)[Q
         if (m < len) p[m] = w[m];
 }
 
-template <int N, bool AV, bool NS, int TX, int TY>
+template <int N, bool AV, bool NS, int TX, int TY, bool PK>
 __global__ void __launch_bounds__(256, 2) stage3z_kernel(const StageArgs A, const Tables<float> Tg)
 {
     using PL = Z3Plan<N, AV, NS, TX, TY>;
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(256, 2) stage3z_kernel(const StageArgs A, cons
     const int N0 = A.N[0], N1 = A.N[1], N2 = A.N[2];
     // stored modes per cell, and the lane's modal x-line (l_y, l_z) = (ly, lz) in the global arrays:
     // tensor storage, or packed total-degree storage (the line's modes l_x <= n - l_y - l_z)
-    const bool packed = A.cmap != nullptr;
+    constexpr bool packed = PK;  // PK: packed total-degree storage (a separate instantiation)
     const int MS = packed ? A.ms : NP;
     const int plen = packed ? max(0, N + 1 - ly - lz) : Q;
     const int poff = packed ? (plen > 0 ? A.cmap[Q * (ly + Q * lz)] : 0) : gl * Q;
@@ -896,11 +896,11 @@ inline void z3_items(int ntx, int nty, int N2, int ctas, int *nzc, int *zchunk)
     }
 }
 
-template <int N, bool AV, bool NS, int TX, int TY>
+template <int N, bool AV, bool NS, int TX, int TY, bool PK>
 cudaError_t run_stage3z(const StageArgs &a_in, const Tables<float> &t, cudaStream_t s, int *grid_out)
 {
     using PL = Z3Plan<N, AV, NS, TX, TY>;
-    auto k = stage3z_kernel<N, AV, NS, TX, TY>;
+    auto k = stage3z_kernel<N, AV, NS, TX, TY, PK>;
     static_assert(PL::BYTES <= 227 * 1024, "z-march plane exceeds shared memory");
     static KernelSetup ks;
     int sms = 0, per_sm = 0;
@@ -928,17 +928,26 @@ cudaError_t run_stage3z(const StageArgs &a_in, const Tables<float> &t, cudaStrea
     return cudaGetLastError();
 }
 
-template <int N>
-cudaError_t run_stage3z_any(const StageArgs &a, const Tables<float> &t, cudaStream_t s, int *grid)
+template <int N, bool PK>
+cudaError_t run_stage3z_variant(const StageArgs &a, const Tables<float> &t, cudaStream_t s, int *grid)
 {
     static_assert(N == 1 || N == 3, "z-march lane groups exist for degrees 1 and 3");
     constexpr int T = N == 1 ? 8 : 4;  // 64 cells per plane at degree 1, 16 at degree 3
     if (a.av_on) {
-        if (a.ns_on) return run_stage3z<N, true, true, T, T>(a, t, s, grid);
-        return run_stage3z<N, true, false, T, T>(a, t, s, grid);
+        if (a.ns_on) return run_stage3z<N, true, true, T, T, PK>(a, t, s, grid);
+        return run_stage3z<N, true, false, T, T, PK>(a, t, s, grid);
     }
-    if (a.ns_on) return run_stage3z<N, false, true, T, T>(a, t, s, grid);
-    return run_stage3z<N, false, false, T, T>(a, t, s, grid);
+    if (a.ns_on) return run_stage3z<N, false, true, T, T, PK>(a, t, s, grid);
+    return run_stage3z<N, false, false, T, T, PK>(a, t, s, grid);
+}
+
+// the packed total-degree variants are instantiated in a translation unit of their own
+// (dgx_inst_3d_packed_f32.cu), compiled in parallel with this one
+template <int N>
+cudaError_t run_stage3z_any(const StageArgs &a, const Tables<float> &t, cudaStream_t s, int *grid)
+{
+    if (a.cmap) return launch_stage3z_packed(N, a, t, s, grid);
+    return run_stage3z_variant<N, false>(a, t, s, grid);
 }
 
 }  // namespace dgx
