@@ -42,7 +42,7 @@ METRIC = "DOF-updates/s per GB300 (FP32-bulk vs FP64, same L1 error) + % HBM roo
 UNIT = "DOF-updates/s"
 FLUSH_BYTES = 256 << 20
 KERNEL_SRCS = [os.path.join(ROOT, "paper_2208_11131_gb300", "csrc", f)
-               for f in ("dgx_internal.h", "dgx_kernels.cuh", "dgx_stage2.cuh", "dgx_stage3z.cuh", "dgx_limiter.cuh",
+               for f in ("dgx_internal.h", "dgx_kernels.cuh", "dgx_stage2.cuh", "dgx_stage3z.cuh", "dgx_stage2t.cuh", "dgx_limiter.cuh",
                          "dgx_inst.cuh", "dgx_inst_2d_f32.cu", "dgx_inst_3d_f32.cu", "dgx_inst_3d_packed_f32.cu", "dgx_inst_3d_f64.cu")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
 

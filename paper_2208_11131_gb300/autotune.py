@@ -15,6 +15,10 @@ per-thread phases.  For every requested degree this tool
    every step), and reports the fastest; ``--write`` puts the winners into the tables.
 
     python -m paper_2208_11131_gb300.autotune --degrees 3 5 [--tracer] [--tiles 6x8,4x8] [--write]
+
+Single simulations of degrees 1 and 3 without a tracer run the 2-D lane-group kernel, whose tile is
+fixed by its lane mapping; the table tiles of those degrees serve the batched kernel.  The tool times
+single simulations, so it skips the plain table at degrees 1 and 3.
 """
 from __future__ import annotations
 
@@ -32,6 +36,8 @@ TU = os.path.join(B.CSRC, "dgx_inst_2d_f32.cu")
 TABLES = ("DGX_TILES", "DGX_TILES_TR")
 # shear-layer cells per axis that give about 4 M conserved DOFs at each degree
 CELLS = {0: 1024, 1: 512, 2: 384, 3: 256, 4: 200, 5: 160}
+# degrees whose single-simulation plans without a tracer run the lane-group kernel (not the tiled one)
+LANE_GROUP_DEGREES = (1, 3)
 _ENTRY = re.compile(r"X\(\s*(\d+)\s*,\s*(\d+)\s*,\s*(\d+)\s*,\s*(\d+)\s*,\s*(\d+)\s*,\s*(\d+)\s*,\s*(\d+)\s*\)")
 
 
@@ -175,6 +181,8 @@ def tune(degrees, tracer: bool, tiles=None, steps: int = 20, warmup: int = 5, re
         os.makedirs(os.path.join(B.BUILD, "tune"), exist_ok=True)
         workdir = tempfile.mkdtemp(prefix="run_", dir=os.path.join(B.BUILD, "tune"))
     plan = {}
+    if not tracer:
+        degrees = [n for n in degrees if n not in LANE_GROUP_DEGREES]
     for n in degrees:
         cur = tables[name][n][:2]
         cands = [tuple(int(v) for v in t.split("x")) for t in tiles] if tiles else candidates(*cur, reach)
@@ -215,7 +223,8 @@ def apply(report: dict, tracer: bool) -> None:
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("--degrees", type=int, nargs="*", default=[0, 1, 2, 3, 4, 5])
+    ap.add_argument("--degrees", type=int, nargs="*", default=[0, 1, 2, 3, 4, 5],
+                    help="degrees to tune (the plain table skips 1 and 3, see above)")
     ap.add_argument("--tracer", action="store_true", help="tune the tiles of the plans with a passive tracer")
     ap.add_argument("--tiles", help="candidate tiles, e.g. 6x8,4x8 (default: the current tile and its neighbours)")
     ap.add_argument("--reach", type=int, default=2, help="neighbour candidates within this many cells per axis")

@@ -15,5 +15,6 @@
     X(0, 16, 16, 1, 16, 16, 1) X(1, 16, 7, 1, 16, 16, 1) X(2, 8, 8, 1, 16, 8, 1) \
     X(3, 6, 6, 1, 16, 8, 1) X(4, 6, 6, 1, 8, 8, 1) X(5, 5, 4, 1, 8, 4, 1)
 #endif
-#define DGX_STAGE_RUN run_stage2_any
+#define DGX_STAGE_RUN run_stage_2d_f32_any
+#include "dgx_stage2t.cuh"
 #include "dgx_inst.cuh"

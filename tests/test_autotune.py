@@ -43,6 +43,6 @@ def test_variant_header_reaches_the_instantiations(tmp_path):
     if out.returncode != 0:
         pytest.skip("nvcc preprocessing unavailable: " + out.stderr[-200:])
     pp = re.sub(r"\s+", "", out.stdout)
-    assert "run_stage2_any<2,3,float,4,9,1,false>" in pp
-    assert "run_stage2_any<2,5,float,3,4,1,true>" in pp
-    assert "run_stage2_any<2,3,float,6,8,1,false>" not in pp
+    assert "run_stage_2d_f32_any<2,3,float,4,9,1,false>" in pp
+    assert "run_stage_2d_f32_any<2,5,float,3,4,1,true>" in pp
+    assert "run_stage_2d_f32_any<2,3,float,6,8,1,false>" not in pp

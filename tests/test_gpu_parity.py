@@ -49,6 +49,9 @@ RHS_CASES = [
     (2, 3, (10, 7), (1.0, 1.0), (1, 1), 0.0, 1),
     (2, 4, (9, 7), (1.0, 1.0), (1, 0), 0.0, 1),
     (2, 5, (6, 5), (1.0, 1.0), (0, 1), 2e-3, 1),
+    # several tiles of the 2-D lane-group kernel (8 x 8 cells at degree 3, 16 x 8 at degree 1), ragged
+    (2, 3, (37, 21), (1.0, 1.5), (0, 1), 1e-3, 1),
+    (2, 1, (45, 19), (1.2, 1.0), (1, 0), 0.0, 1),
     (3, 0, (9, 5, 6), (1.0, 1.0, 1.0), (0, 0, 0), 0.0, 0),
     (3, 1, (7, 5, 3), (1.0, 0.8, 0.6), (0, 0, 0), 1e-3, 1),
     (3, 2, (5, 5, 3), (1.0, 1.0, 1.0), (0, 0, 1), 0.0, 1),
