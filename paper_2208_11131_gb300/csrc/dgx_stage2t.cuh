@@ -326,8 +326,7 @@ __global__ void __launch_bounds__(256, 2) stage2t_kernel(const StageArgs A, cons
             *wig_slot = (float)A.wig[g];
         }
         float by[Q];
-#pragma unroll
-        for (int k = 0; k < Q; ++k) by[k] = tB[ly * Q + (ly ^ k)];
+        xcoef<Q>(tB, ly, by);
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
             float o[Q];
@@ -438,11 +437,8 @@ __global__ void __launch_bounds__(256, 2) stage2t_kernel(const StageArgs A, cons
 #pragma unroll
             for (int f = 0; f < NF; ++f) ld_line<Q, VEC>(slot + f * NP + ly * Q, u[f]);
             float dy[Q], wy[Q];
-#pragma unroll
-            for (int k = 0; k < Q; ++k) {
-                dy[k] = tDn[ly * Q + (ly ^ k)];
-                wy[k] = tWd[ly * Q + (ly ^ k)];
-            }
+            xcoef<Q>(tDn, ly, dy);
+            xcoef<Q>(tWd, ly, wy);
             const float gy = tG[ly];
             const float wig = AV ? sWig[grp] : 0.0f;
             const float *force = static_cast<const float *>(A.force);
@@ -545,8 +541,7 @@ __global__ void __launch_bounds__(256, 2) stage2t_kernel(const StageArgs A, cons
             }
             // nodal -> modal: y across the group's lanes, x in registers
             float cy_[Q];
-#pragma unroll
-            for (int k = 0; k < Q; ++k) cy_[k] = tB[(ly ^ k) * Q + ly];
+            xcoef<Q, true>(tB, ly, cy_);
 #pragma unroll
             for (int f = 0; f < NF; ++f)
 #pragma unroll

@@ -59,15 +59,37 @@ struct Z3Plan {
 };
 
 // Q x Q matrix-vector product across the Q lanes of a group that differ in one index (the lane's
-// index bits selected by STRIDE = 1 (low) or Q (high)): returns sum_k M[i][i ^ k] v(i ^ k) with
-// Mx[k] = M[i][i ^ k] of this lane's index i
+// index bits selected by STRIDE = 1 (low) or Q (high)): out(i) = sum_j M[i][j] v(j), lane i holding
+// v(i).  Recursive doubling: after the first exchange (partner i ^ 1) a lane holds v(i), v(i ^ 1);
+// at Q = 4 it then forms the partial sum that its second partner i ^ 2 needs from those two values
+// and swaps it, so a product takes log2(Q) shuffles and Q multiply-adds.  The lane's coefficients
+// come from xcoef.
 template <int Q, int STRIDE>
 __device__ __forceinline__ float xmatvec(float v, const float (&Mx)[Q])
 {
-    float acc = Mx[0] * v;
-#pragma unroll
-    for (int k = 1; k < Q; ++k) acc = fmaf(Mx[k], __shfl_xor_sync(0xffffffffu, v, k * STRIDE), acc);
-    return acc;
+    static_assert(Q == 2 || Q == 4, "lane products for Q = 2 and 4");
+    const float w = __shfl_xor_sync(0xffffffffu, v, STRIDE);
+    if constexpr (Q == 2) {
+        return fmaf(Mx[1], w, Mx[0] * v);
+    } else {
+        const float part = fmaf(Mx[3], w, Mx[2] * v);  // M[i^2][i] v(i) + M[i^2][i^1] v(i^1)
+        const float recv = __shfl_xor_sync(0xffffffffu, part, 2 * STRIDE);
+        return fmaf(Mx[1], w, fmaf(Mx[0], v, recv));
+    }
+}
+
+// coefficients of lane index i for xmatvec of the Q x Q matrix M (row-major; with T its transpose):
+// M[i][i], M[i][i^1] and, at Q = 4, M[i^2][i], M[i^2][i^1]
+template <int Q, bool T = false>
+__device__ __forceinline__ void xcoef(const float *M, int i, float (&Mx)[Q])
+{
+    auto e = [&](int r, int c) { return T ? M[c * Q + r] : M[r * Q + c]; };
+    Mx[0] = e(i, i);
+    Mx[1] = e(i, i ^ 1);
+    if constexpr (Q == 4) {
+        Mx[2] = e(i ^ 2, i);
+        Mx[3] = e(i ^ 2, i ^ 1);
+    }
 }
 
 // Offset of the x-line (y, z) of one field inside a cell slot.  The Q^2 lines of Q values are
@@ -438,11 +460,8 @@ __global__ void __launch_bounds__(256, 2) stage3z_kernel(const StageArgs A, cons
         // y then z across the group's lanes (xor shuffles): out(i) = sum_m B[i][m] v(m), the lane of
         // index i holding v(i)
         float by[Q], bz[Q];
-#pragma unroll
-        for (int k = 0; k < Q; ++k) {
-            by[k] = tB[ly * Q + (ly ^ k)];
-            bz[k] = tB[lz * Q + (lz ^ k)];
-        }
+        xcoef<Q>(tB, ly, by);
+        xcoef<Q>(tB, lz, bz);
 #pragma unroll
         for (int f = 0; f < NF; ++f)
 #pragma unroll
@@ -469,11 +488,8 @@ __global__ void __launch_bounds__(256, 2) stage3z_kernel(const StageArgs A, cons
             }
             // tangential derivatives of the recovered state: across the group's lanes (all lanes take part)
             float dx[Q], dy[Q];
-#pragma unroll
-            for (int k = 0; k < Q; ++k) {
-                dx[k] = tDn[px * Q + (px ^ k)];
-                dy[k] = tDn[py * Q + (py ^ k)];
-            }
+            xcoef<Q>(tDn, px, dx);
+            xcoef<Q>(tDn, py, dy);
 #pragma unroll
             for (int f = 0; f < NC; ++f) {
                 gtan[0][f] = xmatvec<Q, 1>(ut[f], dx) * K[SK_TWO_H + 0];
@@ -648,13 +664,10 @@ __global__ void __launch_bounds__(256, 2) stage3z_kernel(const StageArgs A, cons
 #pragma unroll
                 for (int f = 0; f < NF; ++f) ld_line<Q, VEC>(slot + f * NP + z3_line<Q>(ly, lz), u[f]);
                 float dy[Q], dz[Q], wy[Q], wz[Q];
-#pragma unroll
-                for (int k = 0; k < Q; ++k) {
-                    dy[k] = tDn[ly * Q + (ly ^ k)];
-                    dz[k] = tDn[lz * Q + (lz ^ k)];
-                    wy[k] = tWd[ly * Q + (ly ^ k)];
-                    wz[k] = tWd[lz * Q + (lz ^ k)];
-                }
+                xcoef<Q>(tDn, ly, dy);
+                xcoef<Q>(tDn, lz, dz);
+                xcoef<Q>(tWd, ly, wy);
+                xcoef<Q>(tWd, lz, wz);
                 const float gy = tG[ly], gz = tG[lz];
                 const float wig = AV ? sWig[cur * TC + grp] : 0.0f;
                 const float *force = static_cast<const float *>(A.force);
@@ -770,11 +783,8 @@ __global__ void __launch_bounds__(256, 2) stage3z_kernel(const StageArgs A, cons
                 }
                 // nodal -> modal: z then y across the group's lanes, out(l) = sum_i B[i][l] r(i); x in registers
                 float cz_[Q], cy_[Q];
-#pragma unroll
-                for (int k = 0; k < Q; ++k) {
-                    cz_[k] = tB[(lz ^ k) * Q + lz];
-                    cy_[k] = tB[(ly ^ k) * Q + ly];
-                }
+                xcoef<Q, true>(tB, lz, cz_);
+                xcoef<Q, true>(tB, ly, cy_);
 #pragma unroll
                 for (int f = 0; f < NF; ++f)
 #pragma unroll
