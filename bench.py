@@ -376,6 +376,23 @@ def step_working_set_bytes(nvals: int, fp32: bool) -> int:
     return nvals * ((8 + 8 + 4 + 4 + 3 * 4) if fp32 else (8 + 8 + 3 * 8))
 
 
+def link_bandwidth(torch, host_in, host_out) -> dict:
+    """host<->device copy rate of one plain pinned copy of the state's size each way (CUDA events on the
+    current stream): the bound of the end-to-end figure's transfers"""
+    dev = torch.empty(host_in.shape, dtype=host_in.dtype, device="cuda")
+    out = {}
+    for name, dst, src in (("h2d_gbs", dev, host_in), ("d2h_gbs", host_out, dev)):
+        dst.copy_(src, non_blocking=True)  # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        dst.copy_(src, non_blocking=True)
+        e1.record()
+        e1.synchronize()
+        out[name] = host_in.numel() * host_in.element_size() / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    del dev
+    return out
+
+
 def stage_roofline(nvals: int, ncell: int, fp32: bool, stage_ms: float, peak_gbs: float) -> dict:
     """HBM roofline of the stage launches of one SSP(5,4) step: algorithmic bytes (every array a stage
     reads once and writes once, plus the per-cell wiggle source) over the summed stage-launch time"""
@@ -630,7 +647,8 @@ def dgx_arm(args, rank, ws, local):
         te = allreduce_max(time.perf_counter() - t0, ws)
         nbytes = a_in.nbytes
         line["e2e"] = {"value": wl.dofs * 5 * e2e_steps * ws / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
-                       "d2h_bytes_per_step": nbytes, "steps": e2e_steps}
+                       "d2h_bytes_per_step": nbytes, "steps": e2e_steps,
+                       "ms_per_step": 1e3 * te / e2e_steps, "link": link_bandwidth(torch, host_in, host_out)}
         del host_in, host_out, a_in, a_out
         # the other precision on the same workload, and the FP32-bulk vs FP64 difference
         other = dgx.Simulation(wl, precision=dgx.DG_FP64 if fp32 else dgx.DG_FP32_BULK)
