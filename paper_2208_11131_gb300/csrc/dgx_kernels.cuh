@@ -353,14 +353,31 @@ __global__ void __launch_bounds__(256) prologue_kernel(const PrologueArgs A, con
     if (tid == 0) s_bad = 0;
     __syncthreads();
     const Real *u = static_cast<const Real *>(A.u);
-    for (int idx = tid; idx < NC * TC * NP; idx += nth) {
-        const int l = idx % NP, fc = idx / NP;
-        const int c = fc % TC, f = fc / TC;
-        const int g = sG[c];
-        // packed total-degree storage: the modes outside the basis are not stored (zero)
-        const int sl = A.cmap ? A.cmap[l] : l;
+    {
+        // the tile's modes, eight loads of a thread in flight at once (the block has 256 threads)
+        constexpr int NL = NC * TC * NP, NTH = 256, PER = (NL + NTH - 1) / NTH, CH = 8;
         const int ms = A.cmap ? A.ms : NP;
-        sU[idx] = (g >= 0 && sl >= 0) ? u[((size_t)f * A.ncell + g) * ms + sl] : Real(0);
+        for (int j0 = 0; j0 < PER; j0 += CH) {
+            Real v[CH];
+#pragma unroll
+            for (int jj = 0; jj < CH; ++jj) {
+                const int idx = tid + NTH * (j0 + jj);
+                v[jj] = Real(0);
+                if (idx < NL) {
+                    const int l = idx % NP, fc = idx / NP;
+                    const int c = fc % TC, f = fc / TC;
+                    const int g = sG[c];
+                    // packed total-degree storage: the modes outside the basis are not stored (zero)
+                    const int sl = A.cmap ? A.cmap[l] : l;
+                    if (g >= 0 && sl >= 0) v[jj] = u[((size_t)f * A.ncell + g) * ms + sl];
+                }
+            }
+#pragma unroll
+            for (int jj = 0; jj < CH; ++jj) {
+                const int idx = tid + NTH * (j0 + jj);
+                if (idx < NL) sU[idx] = v[jj];
+            }
+        }
     }
     __syncthreads();
     if (A.update_sensor) {

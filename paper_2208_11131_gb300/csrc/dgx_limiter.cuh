@@ -55,181 +55,199 @@ __global__ void limiter_kernel(const LimiterArgs A, const Tables<Real> Tg)
     }
     __syncthreads();
 
-    const long long cell = (long long)blockIdx.x * PL::CPB + warp;
-    if (cell >= A.ncell) return;
     const Real *ub = static_cast<const Real *>(A.ubase);
     Real *dl = static_cast<Real *>(A.delta);
     // packed total-degree storage: cmap gives the stored index of a tensor mode (-1: not stored, zero)
     const int ms = A.cmap ? A.ms : NP;
-    for (int i = lane; i < NC * NP; i += 32) {
-        const int f = i / NP, l = i % NP;
-        const int sl = A.cmap ? A.cmap[l] : l;
-        if (sl < 0) {
-            sM[i] = Real(0);
-            continue;
+    // persistent: each warp takes cells in turn, so a cell that needs the full evaluation holds only
+    // its own warp (and that warp's shared memory), not a whole CTA
+    for (long long cell = (long long)blockIdx.x * PL::CPB + warp; cell < A.ncell;
+         cell += (long long)gridDim.x * PL::CPB) {
+        __syncwarp();  // the last cell's write-back has read its shared memory
+        // the cell's modes [field][mode], element i = lane + 32 j in register j of the lane: every
+        // load of the warp in flight at once
+        constexpr int NI = NC * NP, NJ = (NI + 31) / 32;
+        Real w[NJ];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            const int i = lane + 32 * j;
+            w[j] = Real(0);
+            if (i < NI) {
+                const int f = i / NP, l = i % NP;
+                const int sl = A.cmap ? A.cmap[l] : l;
+                if (sl >= 0) {
+                    const size_t gi = ((size_t)f * A.ncell + cell) * ms + sl;
+                    w[j] = A.last ? (Real)A.ufull[gi] : ub[gi] + dl[gi];
+                }
+            }
         }
-        const size_t gi = ((size_t)f * A.ncell + cell) * ms + sl;
-        sM[i] = A.last ? (Real)A.ufull[gi] : ub[gi] + dl[gi];
-    }
-    __syncwarp();
 
-    // A test from the modes alone.  On the reference cell |phi_l| <= c_l = prod_a sqrt(2 l_a + 1), so
-    // every point value of field f lies within w_0 +- V_f, V_f = sum_{l>0} c_l |w_l|.  If the density
-    // and pressure lower bounds of those intervals clear rho_bottom and p_bottom by a margin far above
-    // the rounding of the point evaluation, the evaluation below would find theta = 1 and no halving
-    // at every point -- the case in which it leaves the cell as it is -- so the cell is left now.
-    {
-        const Real gam = (Real)A.gamma;
-        Real var[NC];
+        // A test from the modes alone.  On the reference cell |phi_l| <= c_l = prod_a sqrt(2 l_a + 1), so
+        // every point value of field f lies within w_0 +- V_f, V_f = sum_{l>0} c_l |w_l|.  If the density
+        // and pressure lower bounds of those intervals clear rho_bottom and p_bottom by a margin far above
+        // the rounding of the point evaluation, the evaluation below would find theta = 1 and no halving
+        // at every point -- the case in which it leaves the cell as it is -- so the cell is left now.
+        {
+            const Real gam = (Real)A.gamma;
+            Real var[NC];
 #pragma unroll
-        for (int f = 0; f < NC; ++f) var[f] = Real(0);
-        for (int l = 1 + lane; l < NP; l += 32) {
-            const int l0 = l % Q, l1 = (l / Q) % Q, l2 = DIM == 3 ? l / (Q * Q) : 0;
-            const Real c = sqrt(Real((2 * l0 + 1) * (2 * l1 + 1) * (2 * l2 + 1)));
+            for (int f = 0; f < NC; ++f) var[f] = Real(0);
 #pragma unroll
-            for (int f = 0; f < NC; ++f) var[f] += c * fabs(sM[f * NP + l]);
+            for (int j = 0; j < NJ; ++j) {
+                const int i = lane + 32 * j;
+                const int fi = i / NP, l = i % NP;
+                const int l0 = l % Q, l1 = (l / Q) % Q, l2 = DIM == 3 ? l / (Q * Q) : 0;
+                const Real c = (i < NI && l > 0) ? sqrt(Real((2 * l0 + 1) * (2 * l1 + 1) * (2 * l2 + 1))) : Real(0);
+                const Real t = c * fabs(w[j]);
+#pragma unroll
+                for (int f = 0; f < NC; ++f) var[f] += fi == f ? t : Real(0);
+            }
+#pragma unroll
+            for (int f = 0; f < NC; ++f)
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) var[f] += __shfl_xor_sync(0xffffffffu, var[f], off);
+            Real m[NC];
+#pragma unroll
+            for (int f = 0; f < NC; ++f) m[f] = __shfl_sync(0xffffffffu, w[(f * NP) / 32], (f * NP) % 32);
+            const Real rho_lo = m[0] - var[0];
+            Real mom2 = Real(0);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                const Real mh = fabs(m[1 + a]) + var[1 + a];
+                mom2 += mh * mh;
+            }
+            const Real e_lo = m[DIM + 1] - var[DIM + 1];
+            // floors of Sec. 4.2 from the mean state (as below), and the margins
+            const Real ke_bar = [&] {
+                Real k = Real(0);
+#pragma unroll
+                for (int a = 0; a < DIM; ++a) k += m[1 + a] * m[1 + a];
+                return k;
+            }();
+            const Real p_bar = (gam - Real(1)) * (m[DIM + 1] - Real(0.5) * ke_bar / m[0]);
+            const Real tol = Real(1e-4);
+            bool keep = m[0] > Real(0) && rho_lo - Real(1e-6) * m[0] > tol * (fabs(m[0]) + var[0]);
+            if (keep) {
+                const Real kin = Real(0.5) * mom2 / rho_lo;
+                const Real p_lo = (gam - Real(1)) * (e_lo - kin);
+                keep = p_lo - Real(1e-6) * p_bar > tol * (gam - Real(1)) * (fabs(m[DIM + 1]) + var[DIM + 1] + kin);
+            }
+            // the lanes' butterfly sums may differ in the last bit: lane 0 decides for the warp
+            if (__shfl_sync(0xffffffffu, keep ? 1 : 0, 0)) continue;
         }
 #pragma unroll
-        for (int f = 0; f < NC; ++f)
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) var[f] += __shfl_xor_sync(0xffffffffu, var[f], off);
-        Real m[NC];
-#pragma unroll
-        for (int f = 0; f < NC; ++f) m[f] = sM[f * NP];
-        const Real rho_lo = m[0] - var[0];
-        Real mom2 = Real(0);
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) {
-            const Real mh = fabs(m[1 + a]) + var[1 + a];
-            mom2 += mh * mh;
-        }
-        const Real e_lo = m[DIM + 1] - var[DIM + 1];
-        // floors of Sec. 4.2 from the mean state (as below), and the margins
-        const Real ke_bar = [&] {
-            Real k = Real(0);
-#pragma unroll
-            for (int a = 0; a < DIM; ++a) k += m[1 + a] * m[1 + a];
-            return k;
-        }();
-        const Real p_bar = (gam - Real(1)) * (m[DIM + 1] - Real(0.5) * ke_bar / m[0]);
-        const Real tol = Real(1e-4);
-        bool keep = m[0] > Real(0) && rho_lo - Real(1e-6) * m[0] > tol * (fabs(m[0]) + var[0]);
-        if (keep) {
-            const Real kin = Real(0.5) * mom2 / rho_lo;
-            const Real p_lo = (gam - Real(1)) * (e_lo - kin);
-            keep = p_lo - Real(1e-6) * p_bar > tol * (gam - Real(1)) * (fabs(m[DIM + 1]) + var[DIM + 1] + kin);
-        }
-        // the lanes' butterfly sums may differ in the last bit: lane 0 decides for the warp
-        if (__shfl_sync(0xffffffffu, keep ? 1 : 0, 0)) return;
-    }
+        for (int j = 0; j < NJ; ++j)
+            if (lane + 32 * j < NI) sM[lane + 32 * j] = w[j];
+        __syncwarp();
 
-    // widen axis 0, then 1 (then 2): Q -> E values per line
-    {
-        // pass x: sM [Q^d] -> sA [E * Q^(d-1)]
-        constexpr int LX = NP / Q;
-        for (int i = lane; i < NC * LX * E; i += 32) {
-            const int r = i % E, fl = i / E;
-            const Real *p = sM + fl * Q;
-            Real acc = Real(0);
-#pragma unroll
-            for (int m = 0; m < Q; ++m) acc = fma(tE[r * Q + m], p[m], acc);
-            sA[fl * E + r] = acc;
-        }
-        __syncwarp();
-        // pass y: sA [E, Q, (Q)] -> sB [E, E, (Q)]
-        constexpr int TZ = DIM == 3 ? Q : 1;
-        for (int i = lane; i < NC * E * E * TZ; i += 32) {
-            const int ix = i % E;
-            const int ry = (i / E) % E;
-            const int rest = i / (E * E);  // f * TZ + z
-            const Real *p = sA + rest * (E * Q) + ix;
-            Real acc = Real(0);
-#pragma unroll
-            for (int m = 0; m < Q; ++m) acc = fma(tE[ry * Q + m], p[m * E], acc);
-            sB[rest * (E * E) + ry * E + ix] = acc;
-        }
-        __syncwarp();
-        if (DIM == 3) {
-            // pass z: sB [E, E, Q] -> sA [E, E, E]
-            for (int i = lane; i < NC * NE; i += 32) {
-                const int ixy = i % (E * E);
-                const int rz = (i / (E * E)) % E;
-                const int f = i / NE;
-                const Real *p = sB + f * (E * E * Q) + ixy;
+        // widen axis 0, then 1 (then 2): Q -> E values per line
+        {
+            // pass x: sM [Q^d] -> sA [E * Q^(d-1)]
+            constexpr int LX = NP / Q;
+            for (int i = lane; i < NC * LX * E; i += 32) {
+                const int r = i % E, fl = i / E;
+                const Real *p = sM + fl * Q;
                 Real acc = Real(0);
 #pragma unroll
-                for (int m = 0; m < Q; ++m) acc = fma(tE[rz * Q + m], p[m * E * E], acc);
-                sA[f * NE + rz * E * E + ixy] = acc;
+                for (int m = 0; m < Q; ++m) acc = fma(tE[r * Q + m], p[m], acc);
+                sA[fl * E + r] = acc;
             }
             __syncwarp();
+            // pass y: sA [E, Q, (Q)] -> sB [E, E, (Q)]
+            constexpr int TZ = DIM == 3 ? Q : 1;
+            for (int i = lane; i < NC * E * E * TZ; i += 32) {
+                const int ix = i % E;
+                const int ry = (i / E) % E;
+                const int rest = i / (E * E);  // f * TZ + z
+                const Real *p = sA + rest * (E * Q) + ix;
+                Real acc = Real(0);
+#pragma unroll
+                for (int m = 0; m < Q; ++m) acc = fma(tE[ry * Q + m], p[m * E], acc);
+                sB[rest * (E * E) + ry * E + ix] = acc;
+            }
+            __syncwarp();
+            if (DIM == 3) {
+                // pass z: sB [E, E, Q] -> sA [E, E, E]
+                for (int i = lane; i < NC * NE; i += 32) {
+                    const int ixy = i % (E * E);
+                    const int rz = (i / (E * E)) % E;
+                    const int f = i / NE;
+                    const Real *p = sB + f * (E * E * Q) + ixy;
+                    Real acc = Real(0);
+#pragma unroll
+                    for (int m = 0; m < Q; ++m) acc = fma(tE[rz * Q + m], p[m * E * E], acc);
+                    sA[f * NE + rz * E * E + ixy] = acc;
+                }
+                __syncwarp();
+            }
         }
-    }
-    const Real *pts = DIM == 3 ? sA : sB;  // [NC][NE] values on the widened grid
+        const Real *pts = DIM == 3 ? sA : sB;  // [NC][NE] values on the widened grid
 
-    const Real gamma = (Real)A.gamma;
-    Real mean[NC];
+        const Real gamma = (Real)A.gamma;
+        Real mean[NC];
 #pragma unroll
-    for (int f = 0; f < NC; ++f) mean[f] = sM[f * NP];
-    Real rb, vb[3], pbar, cb;
-    const bool ok_mean = primitives<DIM>(mean, gamma, rb, vb, pbar, cb);
-    const Real rho_b = Real(1e-6) * mean[0], p_b = Real(1e-6) * pbar;
+        for (int f = 0; f < NC; ++f) mean[f] = sM[f * NP];
+        Real rb, vb[3], pbar, cb;
+        const bool ok_mean = primitives<DIM>(mean, gamma, rb, vb, pbar, cb);
+        const Real rho_b = Real(1e-6) * mean[0], p_b = Real(1e-6) * pbar;
 
-    // a point of the widened grid is used when at most one coordinate is at +-1
-    auto used = [&](int i) {
-        const int c0 = i % E, c1 = (i / E) % E, c2 = DIM == 3 ? i / (E * E) : 0;
-        return (c0 >= Q) + (c1 >= Q) + (c2 >= Q) <= 1;
-    };
-    Real rmin = Real(1e30);
-    for (int i = lane; i < NE; i += 32)
-        if (used(i)) rmin = fmin(rmin, pts[i]);
+        // a point of the widened grid is used when at most one coordinate is at +-1
+        auto used = [&](int i) {
+            const int c0 = i % E, c1 = (i / E) % E, c2 = DIM == 3 ? i / (E * E) : 0;
+            return (c0 >= Q) + (c1 >= Q) + (c2 >= Q) <= 1;
+        };
+        Real rmin = Real(1e30);
+        for (int i = lane; i < NE; i += 32)
+            if (used(i)) rmin = fmin(rmin, pts[i]);
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) rmin = fmin(rmin, __shfl_xor_sync(0xffffffffu, rmin, off));
-    const Real theta = rmin < rho_b ? (mean[0] - rho_b) / (mean[0] - rmin) : Real(1);
+        for (int off = 16; off > 0; off >>= 1) rmin = fmin(rmin, __shfl_xor_sync(0xffffffffu, rmin, off));
+        const Real theta = rmin < rho_b ? (mean[0] - rho_b) / (mean[0] - rmin) : Real(1);
 
-    int kmax = 0;
-    bool fail = false;
-    for (int i = lane; i < NE; i += 32) {
-        if (!used(i)) continue;
-        Real dv[NC];
+        int kmax = 0;
+        bool fail = false;
+        for (int i = lane; i < NE; i += 32) {
+            if (!used(i)) continue;
+            Real dv[NC];
 #pragma unroll
-        for (int f = 0; f < NC; ++f) dv[f] = pts[f * NE + i] - mean[f];
-        int k = 0;
-        for (; k <= 60; ++k) {
-            const Real s = ldexp(theta, -k);
-            Real u[NC];
+            for (int f = 0; f < NC; ++f) dv[f] = pts[f * NE + i] - mean[f];
+            int k = 0;
+            for (; k <= 60; ++k) {
+                const Real s = ldexp(theta, -k);
+                Real u[NC];
 #pragma unroll
-            for (int f = 0; f < NC; ++f) u[f] = mean[f] + s * dv[f];
-            Real ke = Real(0);
+                for (int f = 0; f < NC; ++f) u[f] = mean[f] + s * dv[f];
+                Real ke = Real(0);
 #pragma unroll
-            for (int a = 0; a < DIM; ++a) ke += u[1 + a] * u[1 + a];
-            const Real p = (gamma - Real(1)) * (u[DIM + 1] - Real(0.5) * ke / u[0]);
-            if (p >= p_b) break;
+                for (int a = 0; a < DIM; ++a) ke += u[1 + a] * u[1 + a];
+                const Real p = (gamma - Real(1)) * (u[DIM + 1] - Real(0.5) * ke / u[0]);
+                if (p >= p_b) break;
+            }
+            if (k > 60) {
+                fail = true;
+                k = 60;
+            }
+            kmax = max(kmax, k);
         }
-        if (k > 60) {
-            fail = true;
-            k = 60;
-        }
-        kmax = max(kmax, k);
-    }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, off));
-    fail = __any_sync(0xffffffffu, fail);
-    if (lane == 0 && (!ok_mean || fail)) atomicOr(A.status, DG_STATUS_NONPHYS);
-    if (!ok_mean || (theta == Real(1) && kmax == 0)) return;
+        for (int off = 16; off > 0; off >>= 1) kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, off));
+        fail = __any_sync(0xffffffffu, fail);
+        if (lane == 0 && (!ok_mean || fail)) atomicOr(A.status, DG_STATUS_NONPHYS);
+        if (!ok_mean || (theta == Real(1) && kmax == 0)) continue;
 
-    const Real sc = ldexp(theta, -kmax);
-    for (int i = lane; i < NC * NP; i += 32) {
-        const int f = i / NP, l = i % NP;
-        const int sl = A.cmap ? A.cmap[l] : l;
-        if (l == 0 || sl < 0) continue;
-        const size_t gi = ((size_t)f * A.ncell + cell) * ms + sl;
-        if (A.last) {
-            const double u = A.ufull[gi] * (double)sc;
-            A.ufull[gi] = u;
-            if (A.uhi) A.uhi[gi] = (float)u;
-        } else {
-            // limited stage state sc * (u_base + delta), expressed as a new delta over u_base
-            dl[gi] = sc * sM[i] - ub[gi];
+        const Real sc = ldexp(theta, -kmax);
+        for (int i = lane; i < NC * NP; i += 32) {
+            const int f = i / NP, l = i % NP;
+            const int sl = A.cmap ? A.cmap[l] : l;
+            if (l == 0 || sl < 0) continue;
+            const size_t gi = ((size_t)f * A.ncell + cell) * ms + sl;
+            if (A.last) {
+                const double u = A.ufull[gi] * (double)sc;
+                A.ufull[gi] = u;
+                if (A.uhi) A.uhi[gi] = (float)u;
+            } else {
+                // limited stage state sc * (u_base + delta), expressed as a new delta over u_base
+                dl[gi] = sc * sM[i] - ub[gi];
+            }
         }
     }
 }
@@ -240,10 +258,13 @@ cudaError_t run_limiter(const LimiterArgs &a, const Tables<Real> &t, cudaStream_
     using PL = LimiterPlan<DIM, N, Real, TR>;
     auto k = limiter_kernel<DIM, N, Real, TR>;
     static KernelSetup ks;
-    cudaError_t e = kernel_setup(ks, k, 32 * PL::CPB, PL::BYTES);
+    int sms = 0, bps = 0;
+    cudaError_t e = kernel_setup(ks, k, 32 * PL::CPB, PL::BYTES, &sms, &bps);
     if (e != cudaSuccess) return e;
     if (a.ncell == 0) return cudaSuccess;
-    const long long blocks = (a.ncell + PL::CPB - 1) / PL::CPB;
+    // one wave of resident CTAs (persistent warps), fewer when the grid has fewer cells
+    const long long need = (a.ncell + PL::CPB - 1) / PL::CPB;
+    const long long blocks = need < (long long)sms * bps ? need : (long long)sms * bps;
     k<<<(unsigned)blocks, 32 * PL::CPB, PL::BYTES, s>>>(a, t);
     return cudaGetLastError();
 }
