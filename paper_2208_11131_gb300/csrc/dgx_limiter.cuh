@@ -13,6 +13,8 @@
 // scaling by theta and halving k times).
 #pragma once
 
+#include <type_traits>
+
 #include "dgx_kernels.cuh"
 
 namespace dgx {
@@ -31,7 +33,8 @@ struct LimiterPlan {
     static constexpr size_t BYTES = sizeof(Real) * (size_t)(E * Q) + PER_CELL * CPB;
 };
 
-template <int DIM, int N, typename Real, bool TR>
+// LAST: the state is the FP64 u^{n+1} (A.last), else u_base + delta in Real
+template <int DIM, int N, typename Real, bool TR, bool LAST>
 __global__ void limiter_kernel(const LimiterArgs A, const Tables<Real> Tg)
 {
     using PL = LimiterPlan<DIM, N, Real, TR>;
@@ -60,27 +63,45 @@ __global__ void limiter_kernel(const LimiterArgs A, const Tables<Real> Tg)
     // packed total-degree storage: cmap gives the stored index of a tensor mode (-1: not stored, zero)
     const int ms = A.cmap ? A.ms : NP;
     // persistent: each warp takes cells in turn, so a cell that needs the full evaluation holds only
-    // its own warp (and that warp's shared memory), not a whole CTA
-    for (long long cell = (long long)blockIdx.x * PL::CPB + warp; cell < A.ncell;
-         cell += (long long)gridDim.x * PL::CPB) {
-        __syncwarp();  // the last cell's write-back has read its shared memory
-        // the cell's modes [field][mode], element i = lane + 32 j in register j of the lane: every
-        // load of the warp in flight at once
-        constexpr int NI = NC * NP, NJ = (NI + 31) / 32;
-        Real w[NJ];
+    // its own warp (and that warp's shared memory), not a whole CTA.  The loads of a warp's next cell
+    // are issued before the current cell is tested, so they are in flight while it is.
+    // The cell's modes [field][mode]: element i = lane + 32 j in register j of the lane.
+    constexpr int NI = NC * NP, NJ = (NI + 31) / 32;
+    using Raw = typename std::conditional<LAST, double, Real>::type;
+    Raw ra[NJ], rb[NJ];  // raw loads of the next cell: u^{n+1}, or u_base and delta
+    auto fetch = [&](long long c) {
 #pragma unroll
         for (int j = 0; j < NJ; ++j) {
             const int i = lane + 32 * j;
-            w[j] = Real(0);
-            if (i < NI) {
+            ra[j] = Raw(0);
+            rb[j] = Raw(0);
+            if (i < NI && c < A.ncell) {
                 const int f = i / NP, l = i % NP;
                 const int sl = A.cmap ? A.cmap[l] : l;
                 if (sl >= 0) {
-                    const size_t gi = ((size_t)f * A.ncell + cell) * ms + sl;
-                    w[j] = A.last ? (Real)A.ufull[gi] : ub[gi] + dl[gi];
+                    const size_t gi = ((size_t)f * A.ncell + c) * ms + sl;
+                    if constexpr (LAST) {
+                        ra[j] = A.ufull[gi];
+                    } else {
+                        ra[j] = ub[gi];
+                        rb[j] = dl[gi];
+                    }
                 }
             }
         }
+    };
+    // prefetching where the raw registers stay within 40 per thread (the high-degree FP64 plans
+    // load each cell when they reach it)
+    constexpr bool PF = NJ * sizeof(Raw) * (LAST ? 1 : 2) <= 160;
+    const long long stride = (long long)gridDim.x * PL::CPB;
+    if constexpr (PF) fetch((long long)blockIdx.x * PL::CPB + warp);
+    for (long long cell = (long long)blockIdx.x * PL::CPB + warp; cell < A.ncell; cell += stride) {
+        __syncwarp();  // the last cell's write-back has read its shared memory
+        if constexpr (!PF) fetch(cell);
+        Real w[NJ];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) w[j] = LAST ? (Real)ra[j] : Real(ra[j] + rb[j]);
+        if constexpr (PF) fetch(cell + stride);
 
         // A test from the modes alone.  On the reference cell |phi_l| <= c_l = prod_a sqrt(2 l_a + 1), so
         // every point value of field f lies within w_0 +- V_f, V_f = sum_{l>0} c_l |w_l|.  If the density
@@ -240,7 +261,7 @@ __global__ void limiter_kernel(const LimiterArgs A, const Tables<Real> Tg)
             const int sl = A.cmap ? A.cmap[l] : l;
             if (l == 0 || sl < 0) continue;
             const size_t gi = ((size_t)f * A.ncell + cell) * ms + sl;
-            if (A.last) {
+            if (LAST) {
                 const double u = A.ufull[gi] * (double)sc;
                 A.ufull[gi] = u;
                 if (A.uhi) A.uhi[gi] = (float)u;
@@ -256,15 +277,22 @@ template <int DIM, int N, typename Real, bool TR>
 cudaError_t run_limiter(const LimiterArgs &a, const Tables<Real> &t, cudaStream_t s)
 {
     using PL = LimiterPlan<DIM, N, Real, TR>;
-    auto k = limiter_kernel<DIM, N, Real, TR>;
-    static KernelSetup ks;
-    int sms = 0, bps = 0;
-    cudaError_t e = kernel_setup(ks, k, 32 * PL::CPB, PL::BYTES, &sms, &bps);
+    auto k0 = limiter_kernel<DIM, N, Real, TR, false>;
+    auto k1 = limiter_kernel<DIM, N, Real, TR, true>;
+    // both variants are set up on every call (once per device), so the zero-cell launch that handles
+    // make at creation prepares the one that the first step's limiter of u^{n+1} uses as well
+    static KernelSetup ks[2];
+    int sms = 0, bps[2] = {0, 0};
+    cudaError_t e = kernel_setup(ks[0], k0, 32 * PL::CPB, PL::BYTES, &sms, &bps[0]);
     if (e != cudaSuccess) return e;
+    e = kernel_setup(ks[1], k1, 32 * PL::CPB, PL::BYTES, &sms, &bps[1]);
+    if (e != cudaSuccess) return e;
+    auto k = a.last ? k1 : k0;
+    const int bpsm = bps[a.last ? 1 : 0];
     if (a.ncell == 0) return cudaSuccess;
     // one wave of resident CTAs (persistent warps), fewer when the grid has fewer cells
     const long long need = (a.ncell + PL::CPB - 1) / PL::CPB;
-    const long long blocks = need < (long long)sms * bps ? need : (long long)sms * bps;
+    const long long blocks = need < (long long)sms * bpsm ? need : (long long)sms * bpsm;
     k<<<(unsigned)blocks, 32 * PL::CPB, PL::BYTES, s>>>(a, t);
     return cudaGetLastError();
 }
