@@ -354,8 +354,8 @@ __global__ void __launch_bounds__(256) prologue_kernel(const PrologueArgs A, con
     __syncthreads();
     const Real *u = static_cast<const Real *>(A.u);
     {
-        // the tile's modes, eight loads of a thread in flight at once (the block has 256 threads)
-        constexpr int NL = NC * TC * NP, NTH = 256, PER = (NL + NTH - 1) / NTH, CH = 8;
+        // the tile's modes, up to 32 loads of a thread in flight at once (the block has 256 threads)
+        constexpr int NL = NC * TC * NP, NTH = 256, PER = (NL + NTH - 1) / NTH, CH = PER < 32 ? PER : 32;
         const int ms = A.cmap ? A.ms : NP;
         for (int j0 = 0; j0 < PER; j0 += CH) {
             Real v[CH];
@@ -383,19 +383,31 @@ __global__ void __launch_bounds__(256) prologue_kernel(const PrologueArgs A, con
     if (A.update_sensor) {
         const double dt_prev = A.dtp[0];
         const double step = A.dtp[1];
-        for (int c = tid; c < TC; c += nth) {
-            const int g = sG[c];
-            if (g < 0) continue;
+        // TPC threads per cell (a power of two dividing 32) sum strided modes, then combine by shuffles
+        constexpr int TPC0 = 256 / TC < 1 ? 1 : 256 / TC;
+        constexpr int TPC = TPC0 >= 32 ? 32 : TPC0 >= 16 ? 16 : TPC0 >= 8 ? 8 : TPC0 >= 4 ? 4 : TPC0 >= 2 ? 2 : 1;
+        constexpr int CPR = 256 / TPC;  // cells per round of the block
+        for (int c0 = 0; c0 < TC; c0 += CPR) {
+            const int c = c0 + tid / TPC, sub = tid % TPC;
+            const int g = c < TC ? sG[c] : -1;
             Real hi = Real(0), all = Real(0);
-            for (int l = 0; l < NP; ++l) {
-                const Real w = sU[c * NP + l];  // density field (f = 0)
-                const int l0 = l % Q, l1 = (l / Q) % Q, l2 = DIM == 3 ? l / (Q * Q) : 0;
-                // the modes the degree-(n-1) basis lacks (Sec. 4.1)
-                const bool top = N > 0 && (A.total_degree ? (l0 + l1 + l2 == N)
-                                                          : (l0 == N || l1 == N || (DIM == 3 && l2 == N)));
-                all += w * w;
-                if (top) hi += w * w;
+            if (g >= 0) {
+                for (int l = sub; l < NP; l += TPC) {
+                    const Real w = sU[c * NP + l];  // density field (f = 0)
+                    const int l0 = l % Q, l1 = (l / Q) % Q, l2 = DIM == 3 ? l / (Q * Q) : 0;
+                    // the modes the degree-(n-1) basis lacks (Sec. 4.1)
+                    const bool top = N > 0 && (A.total_degree ? (l0 + l1 + l2 == N)
+                                                              : (l0 == N || l1 == N || (DIM == 3 && l2 == N)));
+                    all += w * w;
+                    if (top) hi += w * w;
+                }
             }
+#pragma unroll
+            for (int off = TPC / 2; off > 0; off >>= 1) {
+                all += __shfl_xor_sync(0xffffffffu, all, off);
+                hi += __shfl_xor_sync(0xffffffffu, hi, off);
+            }
+            if (g < 0 || sub != 0) continue;
             const double Sk = all > Real(0) ? (double)(hi / all) : 0.0;
             double dlog = 0.0;
             // S is floored four decades below the onset threshold: below that its value is rounding
