@@ -13,6 +13,10 @@
 #ifndef DGX_TILES_TR
 #define DGX_TILES_TR(X) DGX_TILES(X)
 #endif
+// DGX_PROLOGUE_RUN names the step-prologue dispatch of the unit (run_prologue: the tile prologue)
+#ifndef DGX_PROLOGUE_RUN
+#define DGX_PROLOGUE_RUN run_prologue
+#endif
 
 #define DGX_CAT2(a, b) a##b
 #define DGX_CAT(a, b) DGX_CAT2(a, b)
@@ -27,7 +31,7 @@ namespace dgx {
         return DGX_STAGE_RUN<DGX_DIM, n, DGX_REAL, sx, sy, sz, true>(a, t, s, grid);
 #define DGX_PRO_CASE(n, sx, sy, sz, px, py, pz) \
     case n:                                     \
-        return run_prologue<DGX_DIM, n, DGX_REAL, px, py, pz>(a, t, s);
+        return DGX_PROLOGUE_RUN<DGX_DIM, n, DGX_REAL, px, py, pz>(a, t, s);
 #define DGX_BATCH_CASE(n, sx, sy, sz, px, py, pz) \
     case n:                                      \
         return run_stage2_batch_any<DGX_DIM, n, DGX_REAL, sx, sy, sz>(av, ns, descs, tile_off, nsims, total, t, s);

@@ -964,6 +964,158 @@ cudaError_t run_stage3z_any(const StageArgs &a, const Tables<float> &t, cudaStre
 
 namespace dgx {
 
+// Step prologue of the 3-D FP32-bulk plans of degrees 1 and 3 (runs with the limiter, where it cannot
+// be folded into the first stage): the oscillation sensor and wiggle source of u^n (Sec. 4.1) and the
+// per-CTA maxima of c_s and |v| at the Gauss points for the CFL step.  A cell per lane group, as in
+// the z-marching stage kernel: the cell's modal x-lines in registers, modal -> nodal along x in
+// registers and along y and z by lane products; no shared memory beyond the basis table, so many
+// CTAs are resident and each lane group's loads of its next cell are in flight together.  CTA b
+// takes the cells [b c, (b + 1) c) with c = ceil(ncell / gridDim.x), and writes partial b.
+template <int N>
+__global__ void __launch_bounds__(256) prologue3z_kernel(const PrologueArgs A, const Tables<float> Tg)
+{
+    constexpr int Q = N + 1, NP = Q * Q * Q, G = Q * Q, NC = 5, NTH = 256, NG = NTH / G;
+    constexpr int VEC = (Q * 4) % 16 == 0 ? 16 : 8;
+    __shared__ float tB[Q * Q];
+    __shared__ double red[2][NTH / 32];
+    __shared__ int s_bad;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int gl = lane % G, grp = tid / G;
+    const int ly = gl % Q, lz = gl / Q;
+    for (int i = tid; i < Q * Q; i += NTH) tB[i] = Tg.B[i / Q][i % Q];
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    float by[Q], bz[Q];
+    xcoef<Q>(tB, ly, by);
+    xcoef<Q>(tB, lz, bz);
+    // packed total-degree storage: the lane's modal x-line holds the modes l_x <= n - l_y - l_z
+    const bool packed = A.cmap != nullptr;
+    const int MS = packed ? A.ms : NP;
+    const int plen = packed ? max(0, N + 1 - ly - lz) : Q;
+    const int poff = packed ? (plen > 0 ? A.cmap[Q * (ly + Q * lz)] : 0) : gl * Q;
+    const size_t fstride = (size_t)A.ncell * MS;
+    const float *u = static_cast<const float *>(A.u);
+    const float gamma = (float)A.gamma;
+    const long long cpb = (A.ncell + gridDim.x - 1) / gridDim.x;
+    const long long c0 = (long long)blockIdx.x * cpb;
+    const long long c1 = c0 + cpb < A.ncell ? c0 + cpb : A.ncell;
+    double cmax = 0.0, vmax = 0.0;
+    int bad = 0;
+    for (long long cb = c0; cb < c1; cb += NG) {  // the same trip count in every lane of the CTA
+        const long long g = cb + grp;
+        const bool valid = g < c1;
+        float w[NC][Q];
+        if (valid) {
+            const size_t g0 = (size_t)g * MS + (size_t)poff;
+#pragma unroll
+            for (int f = 0; f < NC; ++f) z3_ld<Q, VEC>(u + g0 + f * fstride, packed, plen, w[f]);
+        } else {
+#pragma unroll
+            for (int f = 0; f < NC; ++f)
+#pragma unroll
+                for (int m = 0; m < Q; ++m) w[f][m] = 0.0f;
+        }
+        if (A.update_sensor) {
+            // sum of squares of the density modes, all and those the degree-(n-1) basis lacks
+            float all = 0.0f, hi = 0.0f;
+#pragma unroll
+            for (int m = 0; m < Q; ++m) {
+                const bool top = A.total_degree ? (m + ly + lz == N) : (m == N || ly == N || lz == N);
+                all += w[0][m] * w[0][m];
+                if (top) hi += w[0][m] * w[0][m];
+            }
+#pragma unroll
+            for (int off = G / 2; off > 0; off >>= 1) {
+                all += __shfl_xor_sync(0xffffffffu, all, off);
+                hi += __shfl_xor_sync(0xffffffffu, hi, off);
+            }
+            if (valid && gl == 0) {
+                const double Sk = all > 0.0f ? (double)(hi / all) : 0.0;
+                const double dt_prev = A.dtp[0], step = A.dtp[1];
+                // S floored four decades below the onset threshold (its logarithm in FP32, as the sensor)
+                const float sf = (float)(1e-4 * A.s_on);
+                double dlog = 0.0;
+                if (step > 0.0 && dt_prev > 0.0)
+                    dlog = (double)((logf(fmaxf((float)Sk, sf)) - logf(fmaxf((float)A.S_prev[g], sf))) /
+                                    (float)dt_prev);
+                A.wig[g] = (Sk > A.s_on) ? A.f_w * fmax(0.0, dlog) : 0.0;
+                A.S_prev[g] = Sk;
+            }
+        }
+        // modal -> nodal: x in registers, then y and z across the group's lanes
+#pragma unroll
+        for (int f = 0; f < NC; ++f) {
+            float o[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int m = 0; m < Q; ++m) acc = fmaf(Tg.B[i][m], w[f][m], acc);
+                o[i] = acc;
+            }
+#pragma unroll
+            for (int i = 0; i < Q; ++i) w[f][i] = xmatvec<Q, Q>(xmatvec<Q, 1>(o[i], by), bz);
+        }
+        if (valid) {
+#pragma unroll
+            for (int x = 0; x < Q; ++x) {
+                float uu[NC], rho, v[3], p, cs;
+#pragma unroll
+                for (int f = 0; f < NC; ++f) uu[f] = w[f][x];
+                if (!primitives<3>(uu, gamma, rho, v, p, cs)) bad = 1;
+                cmax = fmax(cmax, (double)cs);
+                vmax = fmax(vmax, (double)sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
+            }
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, off));
+        vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, off));
+    }
+    if (lane == 0) {
+        red[0][warp] = cmax;
+        red[1][warp] = vmax;
+    }
+    if (bad) s_bad = 1;
+    __syncthreads();
+    if (tid == 0) {
+        double c = 0.0, v = 0.0;
+        for (int w = 0; w < NTH / 32; ++w) {
+            c = fmax(c, red[0][w]);
+            v = fmax(v, red[1][w]);
+        }
+        A.partial[2 * blockIdx.x + 0] = c;
+        A.partial[2 * blockIdx.x + 1] = v;
+        if (s_bad) atomicOr(A.status, DG_STATUS_NONPHYS);
+    }
+}
+
+template <int N>
+cudaError_t run_prologue3z(const PrologueArgs &a, const Tables<float> &t, cudaStream_t s)
+{
+    auto k = prologue3z_kernel<N>;
+    static KernelSetup ks;
+    cudaError_t e = kernel_setup(ks, k, 256, 0);
+    if (e != cudaSuccess) return e;
+    // one partial per tile of the general prologue's tiling (the count the time-step reduction reads)
+    const int blocks = a.ntile[0] * a.ntile[1] * a.ntile[2];
+    if (blocks == 0) return cudaSuccess;
+    k<<<blocks, 256, 0, s>>>(a, t);
+    return cudaGetLastError();
+}
+
+// prologue dispatch of the 3-D FP32-bulk unit: the lane-group prologue for degrees 1 and 3, the
+// general tile prologue otherwise
+template <int DIM, int N, typename Real, int TX, int TY, int TZ>
+cudaError_t run_prologue_3d_f32_any(const PrologueArgs &a, const Tables<Real> &t, cudaStream_t s)
+{
+    if constexpr (DIM == 3 && std::is_same<Real, float>::value && (N == 1 || N == 3))
+        return run_prologue3z<N>(a, t, s);
+    else
+        return run_prologue<DIM, N, Real, TX, TY, TZ>(a, t, s);
+}
+
 // stage dispatch of the 3-D FP32-bulk unit: the z-marching kernel for degrees 1 and 3 without a tracer,
 // the general tile kernel otherwise
 template <int DIM, int N, typename Real, int TX, int TY, int TZ, bool TRACER>
