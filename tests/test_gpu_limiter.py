@@ -30,7 +30,8 @@ def troubled_state(wl, seed):
     return w, cells
 
 
-@pytest.mark.parametrize("dim,n,N", [(2, 2, (9, 7)), (2, 3, (12, 10)), (3, 2, (4, 5, 3)), (3, 3, (4, 3, 3))])
+@pytest.mark.parametrize("dim,n,N", [(2, 2, (9, 7)), (2, 3, (12, 10)), (3, 1, (5, 4, 3)), (3, 2, (4, 5, 3)),
+                                     (3, 3, (4, 3, 3))])
 @pytest.mark.parametrize("prec", [dgx.DG_FP64, dgx.DG_FP32_BULK])
 def test_limited_step_matches_oracle(dim, n, N, prec):
     wl = inputs.Workload("lim", dim, n, tuple(N) + (1,) * (3 - len(N)), (0, 0, 0), (1.0, 1.0, 1.0), gamma=1.4,
@@ -89,3 +90,26 @@ def test_sod_blast_3d_fp32_bulk_tracks_fp64():
     assert rel_l1(wb, wa, 0) < 1e-5
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("n,N", [(1, (6, 5, 4)), (3, (5, 4, 3))])
+def test_limited_cfl_steps_fp32_bulk(n, N):
+    """Three CFL steps with AV and the limiter in FP32-bulk, the time step chosen by each side: the
+    3-D FP32 plans of degrees 1 and 3 run the lane-group step prologue (sensor, wiggle source and
+    the CFL maxima), whose dt must agree with the oracle's to FP32 rounding (relative 1e-5), and the
+    states to the FP32-bulk tolerance."""
+    wl = inputs.Workload("lim", 3, n, N, (0, 0, 0), (1.0, 1.0, 1.0), gamma=1.4, av_on=1, positivity_on=1,
+                         cfl=0.3)
+    w, _ = troubled_state(wl, seed=11 + n)
+    P = problem(wl)
+    ref = oracle.Sim(P, w)
+    sim = dgx.Simulation(wl, precision=dgx.DG_FP32_BULK)
+    sim.set_state(w)
+    for _ in range(3):
+        dt_ref, st = ref.step()
+        assert st == 0
+        sim.step()
+        dt_gpu = sim.get_aux()[2][0]
+        assert abs(dt_gpu - dt_ref) <= 1e-5 * dt_ref
+    assert rel_l1(sim.get_state(), ref.w, 0) < 1e-5
+    sim.close()
