@@ -126,8 +126,10 @@ __global__ void forcing_update_kernel(const ForcingModes fm, int dim, double dec
     }
 }
 
-// one thread per volume node; Q is a compile-time constant, so the node split of the flat index
-// is a multiplication, and the cell split uses 32-bit arithmetic (cells < 2^31)
+// one thread per x-line of Q volume nodes (fixed y and z node of a cell): the y/z phase products of
+// every mode are formed once per line and multiplied by each node's x phase.  Q is a compile-time
+// constant, so the splits of the flat index are multiplications, and the cell split uses 32-bit
+// arithmetic (cells < 2^31)
 template <int DIM, int Q, typename Real>
 __global__ void __launch_bounds__(256) forcing_eval_kernel(int N0, int N1, long long ncell, const Real *tab,
                                                            long long off1, long long off2, const double *smodes,
@@ -135,49 +137,63 @@ __global__ void __launch_bounds__(256) forcing_eval_kernel(int N0, int N1, long 
 {
     constexpr ModeList<DIM> ML = mode_list<DIM>();
     constexpr int NP = DIM == 2 ? Q * Q : Q * Q * Q;
+    constexpr int NL = NP / Q;  // x-lines per cell
     __shared__ Real sm[6 * kForceModes];
     for (int i = threadIdx.x; i < 6 * kForceModes; i += blockDim.x) sm[i] = (Real)smodes[i];
     __syncthreads();
-    const long long total = ncell * NP;
+    const long long total = ncell * NL;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
-        const int cell = (int)(idx / NP);
-        const int j = (int)(idx - (long long)cell * NP);
+        const int cell = (int)(idx / NL);
+        const int line = (int)(idx - (long long)cell * NL);
         const int c01 = cell / N0;
         const int c0 = cell - c01 * N0;
         const int c2 = c01 / N1;
         const int c1 = c01 - c2 * N1;
-        const int j0 = j % Q, j1 = (j / Q) % Q, j2 = j / (Q * Q);
-        // exp(i K_a x_a) for k_a = -2..2 at this node, per axis
-        Real er[3][5], ei[3][5];
-        const Real *t0 = tab + (c0 * Q + j0) * 10;
+        const int j1 = line % Q, j2 = line / Q;
+        // exp(i K_a x_a) for k_a = -2..2 at this line's y and z nodes
+        Real er1[5], ei1[5], er2[5], ei2[5];
         const Real *t1 = tab + off1 + (c1 * Q + j1) * 10;
         const Real *t2 = tab + off2 + (c2 * Q + j2) * 10;
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-            er[0][k] = t0[2 * k];
-            ei[0][k] = t0[2 * k + 1];
-            er[1][k] = t1[2 * k];
-            ei[1][k] = t1[2 * k + 1];
-            er[2][k] = DIM == 3 ? t2[2 * k] : Real(1);
-            ei[2][k] = DIM == 3 ? t2[2 * k + 1] : Real(0);
+            er1[k] = t1[2 * k];
+            ei1[k] = t1[2 * k + 1];
+            er2[k] = DIM == 3 ? t2[2 * k] : Real(1);
+            ei2[k] = DIM == 3 ? t2[2 * k + 1] : Real(0);
         }
-        Real s[3] = {Real(0), Real(0), Real(0)};
+        // y/z part of every mode's phase
+        Real pr[ML.n], pi[ML.n];
 #pragma unroll
         for (int m = 0; m < ML.n; ++m) {
-            const int kx = ML.k[m][0] + 2, ky = ML.k[m][1] + 2, kz = ML.k[m][2] + 2;
-            Real re = er[0][kx] * er[1][ky] - ei[0][kx] * ei[1][ky];
-            Real im = er[0][kx] * ei[1][ky] + ei[0][kx] * er[1][ky];
-            if (DIM == 3) {
-                const Real r2 = re * er[2][kz] - im * ei[2][kz];
-                im = re * ei[2][kz] + im * er[2][kz];
-                re = r2;
+            const int ky = ML.k[m][1] + 2, kz = ML.k[m][2] + 2;
+            pr[m] = er1[ky] * er2[kz] - ei1[ky] * ei2[kz];
+            pi[m] = er1[ky] * ei2[kz] + ei1[ky] * er2[kz];
+        }
+        Real *o0 = out + (long long)cell * NP + (long long)line * Q;
+        // one x node at a time (the amplitudes are re-read from shared memory per node rather than
+        // held in registers for the whole line)
+#pragma unroll 1
+        for (int x = 0; x < Q; ++x) {
+            const Real *t0 = tab + (c0 * Q + x) * 10;
+            Real er0[5], ei0[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                er0[k] = t0[2 * k];
+                ei0[k] = t0[2 * k + 1];
+            }
+            Real s[3] = {Real(0), Real(0), Real(0)};
+#pragma unroll
+            for (int m = 0; m < ML.n; ++m) {
+                const int kx = ML.k[m][0] + 2;
+                const Real re = er0[kx] * pr[m] - ei0[kx] * pi[m];
+                const Real im = er0[kx] * pi[m] + ei0[kx] * pr[m];
+#pragma unroll
+                for (int a = 0; a < DIM; ++a) s[a] += sm[6 * m + a] * re - sm[6 * m + 3 + a] * im;
             }
 #pragma unroll
-            for (int a = 0; a < DIM; ++a) s[a] += sm[6 * m + a] * re - sm[6 * m + 3 + a] * im;
+            for (int a = 0; a < DIM; ++a) o0[(long long)a * ncell * NP + x] = s[a];
         }
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) out[((long long)a * ncell + cell) * NP + j] = s[a];
     }
 }
 
@@ -186,7 +202,7 @@ cudaError_t launch_eval(const int *N, long long ncell, const Real *tab, const lo
                         Real *out, cudaStream_t s)
 {
     constexpr int NP = DIM == 2 ? Q * Q : Q * Q * Q;
-    const long long total = ncell * NP;
+    const long long total = ncell * (NP / Q);
     long long blocks = (total + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) return cudaSuccess;
